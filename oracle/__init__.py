@@ -1,0 +1,171 @@
+"""FP64 CPU oracle for the Wilson-clover propagator path (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU-baseline leg, never by the library.  The arithmetic lives in
+``oracle.c`` (plain C, FP64, single thread); this wrapper only compiles it and
+marshals numpy arrays.  Every function documents the paper passage it follows
+in ``oracle.c``.
+
+Layouts (shared with the library's host ABI): gauge ``U[t,z,y,x,mu,3,3]``,
+spinor ``psi[t,z,y,x,spin,colour]``, complex128; ``dims = (Lx, Ly, Lz, T)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+DEFAULT_THETA = (1.0, 1.0, 1.0, -1.0)
+
+
+def build(force: bool = False) -> str:
+    """Compiles oracle.c into _build/liboracle.so with gcc (no GPU needed)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lp = ctypes.POINTER(ctypes.c_long)
+        lib.oracle_gamma.argtypes = [ctypes.c_int, dp]
+        lib.oracle_field_strength.argtypes = [ip, dp, dp]
+        lib.oracle_dirac.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, ctypes.c_int]
+        lib.oracle_dirac_many.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, ctypes.c_long, dp, dp,
+                                          ctypes.c_int]
+        lib.oracle_dirac_sites.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp,
+                                           ctypes.c_long, lp, dp]
+        lib.oracle_cgnr.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                    ctypes.c_double, ctypes.c_int, ip, dp]
+        lib.oracle_cgnr.restype = ctypes.c_int
+        lib.oracle_pion_contract.argtypes = [ip, dp, ctypes.c_int, dp]
+        lib.oracle_pion.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.c_double, ctypes.c_int, dp, dp, ip, dp]
+        lib.oracle_pion.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _dims(dims):
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+    assert d.shape == (4,)
+    return d
+
+
+def _theta(theta):
+    th = np.asarray(theta, dtype=np.complex128)
+    assert th.shape == (4,)
+    return np.ascontiguousarray(th)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def gamma(mu: int) -> np.ndarray:
+    """gamma_mu (mu = 0..3 = x,y,z,t) or gamma5 (mu = 4) as a 4x4 complex matrix."""
+    out = np.zeros((4, 4), dtype=np.complex128)
+    _load().oracle_gamma(mu, _dp(out))
+    return out
+
+
+def field_strength(dims, U) -> np.ndarray:
+    """Clover field F_{mu nu}(x), shape (T,Z,Y,X,6,3,3), planes xy xz xt yz yt zt."""
+    lx, ly, lz, lt = dims
+    U = _c128(U)
+    out = np.zeros((lt, lz, ly, lx, 6, 3, 3), dtype=np.complex128)
+    d = _dims(dims)
+    _load().oracle_field_strength(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), _dp(out))
+    return out
+
+
+def dirac(dims, U, kappa, csw, psi, theta=DEFAULT_THETA, dagger=False) -> np.ndarray:
+    """Full-lattice D psi (or D^dag psi) in FP64."""
+    U, psi, th, d = _c128(U), _c128(psi), _theta(theta), _dims(dims)
+    out = np.zeros_like(psi)
+    _load().oracle_dirac(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw,
+                         _dp(th), _dp(psi), _dp(out), int(bool(dagger)))
+    return out
+
+
+def dirac_matrix(dims, U, kappa, csw, theta=DEFAULT_THETA, dagger=False) -> np.ndarray:
+    """Dense matrix of D (or D^dag), shape (12V, 12V), built column by column."""
+    U, th, d = _c128(U), _theta(theta), _dims(dims)
+    n = 12 * int(np.prod(dims))
+    eye = np.eye(n, dtype=np.complex128)
+    out = np.zeros_like(eye)
+    _load().oracle_dirac_many(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, _dp(th),
+                              n, _dp(eye), _dp(out), int(bool(dagger)))
+    return out.T.copy()
+
+
+def dirac_sites(dims, U, kappa, csw, psi, sites, theta=DEFAULT_THETA) -> np.ndarray:
+    """(D psi)(x) at the lexicographic site indices ``sites``, shape (n, 4, 3)."""
+    U, psi, th, d = _c128(U), _c128(psi), _theta(theta), _dims(dims)
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    out = np.zeros((len(s), 4, 3), dtype=np.complex128)
+    _load().oracle_dirac_sites(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw,
+                               _dp(th), _dp(psi), len(s), s.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                               _dp(out))
+    return out
+
+
+def cgnr(dims, U, kappa, csw, b, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000, x0=None):
+    """Solves D x = b by CGNR to true relative residual ``tol``.
+
+    Returns (x, iterations, true relative residual, converged).
+    """
+    U, b, th, d = _c128(U), _c128(b), _theta(theta), _dims(dims)
+    x = np.zeros_like(b) if x0 is None else _c128(x0).copy()
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0)
+    st = _load().oracle_cgnr(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, _dp(th),
+                             _dp(b), _dp(x), tol, maxiter, ctypes.byref(it), ctypes.byref(res))
+    return x, it.value, res.value, st == 0
+
+
+def pion_contract(dims, prop, src_t) -> np.ndarray:
+    """C(t) from 12 propagator columns prop[j, t, z, y, x, spin, colour]."""
+    prop, d = _c128(prop), _dims(dims)
+    out = np.zeros(dims[3])
+    _load().oracle_pion_contract(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(prop), int(src_t),
+                                 _dp(out))
+    return out
+
+
+def pion(dims, U, kappa, csw, src, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000, want_prop=False):
+    """Point-source propagator (12 columns) and pion C(t).
+
+    Returns (corr, prop or None, iterations[12], residuals[12], failed_columns).
+    """
+    lx, ly, lz, lt = dims
+    U, th, d = _c128(U), _theta(theta), _dims(dims)
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+    corr = np.zeros(lt)
+    prop = np.zeros((12, lt, lz, ly, lx, 4, 3), dtype=np.complex128) if want_prop else None
+    iters = np.zeros(12, dtype=np.int32)
+    res = np.zeros(12)
+    failed = _load().oracle_pion(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, _dp(th),
+                                 s.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), tol, maxiter, _dp(corr),
+                                 _dp(prop) if prop is not None else None,
+                                 iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(res))
+    return corr, prop, iters, res, failed

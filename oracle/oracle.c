@@ -1,0 +1,610 @@
+/*
+ * FP64 CPU oracle for the O(a)-improved (clover) Wilson propagator path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU library computes.  Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load it; the library never calls
+ * it and shares no code, header, table or helper with it.
+ *
+ * What it follows (LatticeGPU.jl, arXiv:2503.16994):
+ *   - Sec. 3.3: DiracParam(m0, csw, theta, ...), Dw! (the Wilson-clover
+ *     operator), Csw! (the Sheikholeslami-Wohlert term stored as a clover
+ *     field and added at every application), CG! and propagator! (point
+ *     source of given spin, colour and position), and the footnote there
+ *     that theta holds the full boundary phase factors.
+ *   - Sec. 2.1: lattice extents with time last.
+ *   - Sec. 2.2: SU(3) links and 4-spinor x 3-colour fermion fields.
+ * The paper prints no formula for the operator.  The reading used here is
+ * the standard kappa-normalised O(a)-improved Wilson operator:
+ *
+ *   (D psi)(x) = psi(x)
+ *       - kappa sum_mu [ (1 - g_mu) U~_mu(x) psi(x+mu)
+ *                        + (1 + g_mu) U~_mu(x-mu)^dag psi(x-mu) ]
+ *       + i kappa csw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x) psi(x)
+ *
+ * with U~_mu(x) = theta_mu U_mu(x) on the link that leaves the last slice in
+ * direction mu (x_mu = L_mu - 1), sigma_{mu nu} = (i/2)[g_mu, g_nu], and
+ * F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^dag)/8 made traceless, Q being the sum of
+ * the four plaquette leaves around x (the clover).  Gamma matrices are in the
+ * chiral basis: g_t = [[0,-1],[-1,0]], g_k = [[0,-i s_k],[i s_k,0]] in 2x2
+ * spin blocks, so g5 = g_t g_x g_y g_z = diag(1,1,-1,-1).
+ *
+ * Layouts (host, lexicographic with x fastest and t slowest, mu = 0..3 =
+ * x,y,z,t): gauge U[site][mu][a][b], spinor psi[site][spin][colour], complex
+ * numbers as interleaved (re, im) doubles.
+ *
+ * Parity pins for every function here live in tests/test_oracle_pins.py.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* Lattice geometry (Sec. 2.1: iL with the time extent last)           */
+/* ------------------------------------------------------------------ */
+
+static long volume_of(const int L[4]) { return (long)L[0] * L[1] * L[2] * L[3]; }
+
+static void coords_of(const int L[4], long s, int x[4])
+{
+    for (int mu = 0; mu < 4; ++mu) {
+        x[mu] = (int)(s % L[mu]);
+        s /= L[mu];
+    }
+}
+
+static long index_of(const int L[4], const int x[4])
+{
+    return x[0] + (long)L[0] * (x[1] + (long)L[1] * (x[2] + (long)L[2] * x[3]));
+}
+
+/* site reached from s by one step of dir = +1 or -1 in direction mu */
+static long step(const int L[4], long s, int mu, int dir)
+{
+    int x[4];
+    coords_of(L, s, x);
+    x[mu] = (x[mu] + dir + L[mu]) % L[mu];
+    return index_of(L, x);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gamma matrices in the chiral basis, built from the Pauli matrices    */
+/* ------------------------------------------------------------------ */
+
+static cplx G[5][4][4];     /* g_x, g_y, g_z, g_t, g5 */
+static cplx SIGMA[4][4][4][4]; /* sigma_{mu nu} = (i/2)[g_mu, g_nu] */
+static int gamma_ready = 0;
+
+static void init_gamma(void)
+{
+    if (gamma_ready) return;
+    const cplx pauli[3][2][2] = {
+        {{0, 1}, {1, 0}},
+        {{0, -I}, {I, 0}},
+        {{1, 0}, {0, -1}},
+    };
+    memset(G, 0, sizeof G);
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                G[k][i][2 + j] = -I * pauli[k][i][j];
+                G[k][2 + i][j] = I * pauli[k][i][j];
+            }
+    for (int i = 0; i < 2; ++i) {
+        G[3][i][2 + i] = -1;
+        G[3][2 + i][i] = -1;
+    }
+    /* g5 = g_t g_x g_y g_z */
+    cplx a[4][4], b[4][4];
+    memcpy(a, G[3], sizeof a);
+    for (int k = 0; k < 3; ++k) {
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                cplx acc = 0;
+                for (int l = 0; l < 4; ++l) acc += a[i][l] * G[k][l][j];
+                b[i][j] = acc;
+            }
+        memcpy(a, b, sizeof a);
+    }
+    memcpy(G[4], a, sizeof a);
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = 0; nu < 4; ++nu)
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    cplx c = 0;
+                    for (int l = 0; l < 4; ++l)
+                        c += G[mu][i][l] * G[nu][l][j] - G[nu][i][l] * G[mu][l][j];
+                    SIGMA[mu][nu][i][j] = 0.5 * I * c;
+                }
+    gamma_ready = 1;
+}
+
+/* gamma matrix mu (0..3 = x,y,z,t; 4 = gamma5) as 4x4 complex, row-major */
+void oracle_gamma(int mu, double *out)
+{
+    init_gamma();
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            out[2 * (4 * i + j)] = creal(G[mu][i][j]);
+            out[2 * (4 * i + j) + 1] = cimag(G[mu][i][j]);
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* 3x3 complex matrices (Sec. 2.2: SU(3) link variables)               */
+/* ------------------------------------------------------------------ */
+
+typedef struct { cplx m[3][3]; } mat3;
+
+static mat3 link_at(const double *U, long s, int mu)
+{
+    mat3 r;
+    const double *p = U + 18 * (4 * s + mu);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) r.m[a][b] = p[2 * (3 * a + b)] + I * p[2 * (3 * a + b) + 1];
+    return r;
+}
+
+static mat3 mul(mat3 a, mat3 b)
+{
+    mat3 r;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cplx c = 0;
+            for (int k = 0; k < 3; ++k) c += a.m[i][k] * b.m[k][j];
+            r.m[i][j] = c;
+        }
+    return r;
+}
+
+static mat3 dag(mat3 a)
+{
+    mat3 r;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) r.m[i][j] = conj(a.m[j][i]);
+    return r;
+}
+
+static mat3 add(mat3 a, mat3 b)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) a.m[i][j] += b.m[i][j];
+    return a;
+}
+
+/* ------------------------------------------------------------------ */
+/* Clover field (Sec. 3.3, Csw!): F_{mu nu}(x) for the 6 planes mu<nu   */
+/* ------------------------------------------------------------------ */
+
+/* Sum of the four plaquette leaves in the (mu, nu) plane that start and end
+ * at x, all with the same orientation (mu first, then nu). */
+static mat3 clover_leaves(const int L[4], const double *U, long x, int mu, int nu)
+{
+    long xpm = step(L, x, mu, +1), xpn = step(L, x, nu, +1);
+    long xmm = step(L, x, mu, -1), xmn = step(L, x, nu, -1);
+    long xmm_pn = step(L, xmm, nu, +1);  /* x - mu + nu */
+    long xmm_mn = step(L, xmm, nu, -1);  /* x - mu - nu */
+    long xpm_mn = step(L, xpm, nu, -1);  /* x + mu - nu */
+
+    /* x -> x+mu -> x+mu+nu -> x+nu -> x */
+    mat3 q1 = mul(mul(link_at(U, x, mu), link_at(U, xpm, nu)),
+                  mul(dag(link_at(U, xpn, mu)), dag(link_at(U, x, nu))));
+    /* x -> x+nu -> x+nu-mu -> x-mu -> x */
+    mat3 q2 = mul(mul(link_at(U, x, nu), dag(link_at(U, xmm_pn, mu))),
+                  mul(dag(link_at(U, xmm, nu)), link_at(U, xmm, mu)));
+    /* x -> x-mu -> x-mu-nu -> x-nu -> x */
+    mat3 q3 = mul(mul(dag(link_at(U, xmm, mu)), dag(link_at(U, xmm_mn, nu))),
+                  mul(link_at(U, xmm_mn, mu), link_at(U, xmn, nu)));
+    /* x -> x-nu -> x-nu+mu -> x+mu -> x */
+    mat3 q4 = mul(mul(dag(link_at(U, xmn, nu)), link_at(U, xmn, mu)),
+                  mul(link_at(U, xpm_mn, nu), dag(link_at(U, x, mu))));
+    return add(add(q1, q2), add(q3, q4));
+}
+
+/* F_{mu nu}(x) = (Q - Q^dag)/8, then made traceless */
+static mat3 field_strength(const int L[4], const double *U, long x, int mu, int nu)
+{
+    mat3 q = clover_leaves(L, U, x, mu, nu);
+    mat3 f;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) f.m[i][j] = (q.m[i][j] - conj(q.m[j][i])) / 8.0;
+    cplx tr = (f.m[0][0] + f.m[1][1] + f.m[2][2]) / 3.0;
+    for (int i = 0; i < 3; ++i) f.m[i][i] -= tr;
+    return f;
+}
+
+/* The six planes in the order (x,y) (x,z) (x,t) (y,z) (y,t) (z,t). */
+static const int PLANE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+/* F[site][plane][3][3] complex for all sites (the stored clover field). */
+void oracle_field_strength(const int *L, const double *U, double *F)
+{
+    long V = volume_of(L);
+    for (long x = 0; x < V; ++x)
+        for (int p = 0; p < 6; ++p) {
+            mat3 f = field_strength(L, U, x, PLANE[p][0], PLANE[p][1]);
+            double *o = F + 18 * (6 * x + p);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    o[2 * (3 * a + b)] = creal(f.m[a][b]);
+                    o[2 * (3 * a + b) + 1] = cimag(f.m[a][b]);
+                }
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* The Dirac operator (Sec. 3.3, Dw!)                                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct { cplx c[4][3]; } spinor;
+
+static spinor spinor_at(const double *psi, long s)
+{
+    spinor r;
+    const double *p = psi + 24 * s;
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) r.c[al][a] = p[2 * (3 * al + a)] + I * p[2 * (3 * al + a) + 1];
+    return r;
+}
+
+static void spinor_store(double *psi, long s, const spinor *v)
+{
+    double *p = psi + 24 * s;
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) {
+            p[2 * (3 * al + a)] = creal(v->c[al][a]);
+            p[2 * (3 * al + a) + 1] = cimag(v->c[al][a]);
+        }
+}
+
+/* colour matrix m acting on every spin component, times a scalar phase */
+static spinor colour_mul(mat3 m, cplx phase, spinor v)
+{
+    spinor r;
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) {
+            cplx c = 0;
+            for (int b = 0; b < 3; ++b) c += m.m[a][b] * v.c[al][b];
+            r.c[al][a] = phase * c;
+        }
+    return r;
+}
+
+/* out += coef * (1 + sgn g_mu) v */
+static void add_projected(spinor *out, cplx coef, int sgn, int mu, const spinor *v)
+{
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) {
+            cplx c = v->c[al][a];
+            for (int be = 0; be < 4; ++be) c += sgn * G[mu][al][be] * v->c[be][a];
+            out->c[al][a] += coef * c;
+        }
+}
+
+typedef struct {
+    int L[4];
+    const double *U;
+    double kappa, csw;
+    cplx theta[4];
+    double *F; /* clover field F[site][plane][3][3], NULL when csw == 0 */
+} dirac_ctx;
+
+static void ctx_init(dirac_ctx *c, const int *L, const double *U, double kappa, double csw,
+                     const double *theta)
+{
+    init_gamma();
+    memcpy(c->L, L, sizeof c->L);
+    c->U = U;
+    c->kappa = kappa;
+    c->csw = csw;
+    for (int mu = 0; mu < 4; ++mu) c->theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
+    c->F = NULL;
+    if (csw != 0.0) {
+        c->F = malloc(sizeof(double) * 108 * volume_of(L));
+        oracle_field_strength(L, U, c->F);
+    }
+}
+
+static void ctx_free(dirac_ctx *c) { free(c->F); c->F = NULL; }
+
+static mat3 stored_F(const dirac_ctx *c, long x, int p)
+{
+    mat3 f;
+    const double *q = c->F + 18 * (6 * x + p);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) f.m[a][b] = q[2 * (3 * a + b)] + I * q[2 * (3 * a + b) + 1];
+    return f;
+}
+
+/* (D psi)(x) for one site x */
+static spinor dirac_site(const dirac_ctx *c, const double *psi, long x)
+{
+    const int *L = c->L;
+    int xc[4];
+    coords_of(L, x, xc);
+    spinor out = spinor_at(psi, x);
+    for (int mu = 0; mu < 4; ++mu) {
+        /* forward: -kappa (1 - g_mu) U~_mu(x) psi(x+mu) */
+        long y = step(L, x, mu, +1);
+        cplx ph = (xc[mu] == L[mu] - 1) ? c->theta[mu] : 1.0;
+        spinor v = colour_mul(link_at(c->U, x, mu), ph, spinor_at(psi, y));
+        add_projected(&out, -c->kappa, -1, mu, &v);
+        /* backward: -kappa (1 + g_mu) U~_mu(x-mu)^dag psi(x-mu) */
+        y = step(L, x, mu, -1);
+        ph = (xc[mu] == 0) ? conj(c->theta[mu]) : 1.0;
+        v = colour_mul(dag(link_at(c->U, y, mu)), ph, spinor_at(psi, y));
+        add_projected(&out, -c->kappa, +1, mu, &v);
+    }
+    if (c->F) {
+        /* + i kappa csw sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(x) psi(x) */
+        spinor s = spinor_at(psi, x);
+        for (int p = 0; p < 6; ++p) {
+            int mu = PLANE[p][0], nu = PLANE[p][1];
+            spinor fs = colour_mul(stored_F(c, x, p), 1.0, s);
+            for (int al = 0; al < 4; ++al)
+                for (int a = 0; a < 3; ++a) {
+                    cplx acc = 0;
+                    for (int be = 0; be < 4; ++be) acc += SIGMA[mu][nu][al][be] * fs.c[be][a];
+                    out.c[al][a] += I * c->kappa * c->csw * acc;
+                }
+        }
+    }
+    return out;
+}
+
+static void dirac_apply(const dirac_ctx *c, const double *in, double *out)
+{
+    long V = volume_of(c->L);
+    for (long x = 0; x < V; ++x) {
+        spinor r = dirac_site(c, in, x);
+        spinor_store(out, x, &r);
+    }
+}
+
+/* D^dag by definition: every term D(x, y) of the operator adds its conjugate
+ * transpose D(x, y)^dag psi(x) into out(y).  Gamma matrices are Hermitian, so
+ * (1 -/+ g_mu)^dag = (1 -/+ g_mu); the clover term is Hermitian. */
+static void dirac_dagger_apply(const dirac_ctx *c, const double *in, double *out)
+{
+    const int *L = c->L;
+    long V = volume_of(L);
+    spinor *acc = calloc((size_t)V, sizeof(spinor));
+    for (long x = 0; x < V; ++x) {
+        int xc[4];
+        coords_of(L, x, xc);
+        spinor px = spinor_at(in, x);
+        /* diagonal: 1 + clover^dag */
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) acc[x].c[al][a] += px.c[al][a];
+        if (c->F) {
+            for (int p = 0; p < 6; ++p) {
+                int mu = PLANE[p][0], nu = PLANE[p][1];
+                /* (i k csw sigma (x) F)^dag = -i k csw sigma (x) F^dag */
+                spinor fs = colour_mul(dag(stored_F(c, x, p)), 1.0, px);
+                for (int al = 0; al < 4; ++al)
+                    for (int a = 0; a < 3; ++a) {
+                        cplx s = 0;
+                        for (int be = 0; be < 4; ++be) s += conj(SIGMA[mu][nu][be][al]) * fs.c[be][a];
+                        acc[x].c[al][a] += -I * c->kappa * c->csw * s;
+                    }
+            }
+        }
+        for (int mu = 0; mu < 4; ++mu) {
+            /* term D(x, x+mu) = -kappa (1 - g_mu) U~_mu(x): adjoint goes to x+mu */
+            long y = step(L, x, mu, +1);
+            cplx ph = (xc[mu] == L[mu] - 1) ? c->theta[mu] : 1.0;
+            spinor v = colour_mul(dag(link_at(c->U, x, mu)), conj(ph), px);
+            add_projected(&acc[y], -c->kappa, -1, mu, &v);
+            /* term D(x, x-mu) = -kappa (1 + g_mu) U~_mu(x-mu)^dag: adjoint to x-mu */
+            y = step(L, x, mu, -1);
+            ph = (xc[mu] == 0) ? conj(c->theta[mu]) : 1.0;
+            v = colour_mul(link_at(c->U, y, mu), conj(ph), px);
+            add_projected(&acc[y], -c->kappa, +1, mu, &v);
+        }
+    }
+    for (long x = 0; x < V; ++x) spinor_store(out, x, &acc[x]);
+    free(acc);
+}
+
+/* theta: 4 complex boundary phase factors as (re, im) pairs */
+void oracle_dirac(const int *L, const double *U, double kappa, double csw, const double *theta,
+                  const double *in, double *out, int dagger)
+{
+    dirac_ctx c;
+    ctx_init(&c, L, U, kappa, csw, theta);
+    if (dagger)
+        dirac_dagger_apply(&c, in, out);
+    else
+        dirac_apply(&c, in, out);
+    ctx_free(&c);
+}
+
+/* D (or D^dag) applied to n fields stored one after another (used to build
+ * the dense matrix of D on tiny lattices column by column). */
+void oracle_dirac_many(const int *L, const double *U, double kappa, double csw, const double *theta,
+                       long n, const double *in, double *out, int dagger)
+{
+    dirac_ctx c;
+    ctx_init(&c, L, U, kappa, csw, theta);
+    long len = 24 * volume_of(L);
+    for (long k = 0; k < n; ++k) {
+        if (dagger)
+            dirac_dagger_apply(&c, in + k * len, out + k * len);
+        else
+            dirac_apply(&c, in + k * len, out + k * len);
+    }
+    ctx_free(&c);
+}
+
+/* (D psi)(x) at the listed sites only: out[k] is the 12-component spinor at
+ * sites[k].  The clover term is computed at those sites only, so this works
+ * on large lattices where a full application would be slow. */
+void oracle_dirac_sites(const int *L, const double *U, double kappa, double csw,
+                        const double *theta, const double *in, long nsites, const long *sites,
+                        double *out)
+{
+    dirac_ctx c;
+    init_gamma();
+    memcpy(c.L, L, sizeof c.L);
+    c.U = U;
+    c.kappa = kappa;
+    c.csw = csw;
+    for (int mu = 0; mu < 4; ++mu) c.theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
+    double Fx[108];
+    for (long k = 0; k < nsites; ++k) {
+        long x = sites[k];
+        c.F = NULL;
+        spinor r = dirac_site(&c, in, x);
+        if (csw != 0.0) {
+            spinor s = spinor_at(in, x);
+            for (int p = 0; p < 6; ++p) {
+                mat3 f = field_strength(L, U, x, PLANE[p][0], PLANE[p][1]);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        Fx[18 * p + 2 * (3 * a + b)] = creal(f.m[a][b]);
+                        Fx[18 * p + 2 * (3 * a + b) + 1] = cimag(f.m[a][b]);
+                    }
+            }
+            for (int p = 0; p < 6; ++p) {
+                int mu = PLANE[p][0], nu = PLANE[p][1];
+                mat3 f;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        f.m[a][b] = Fx[18 * p + 2 * (3 * a + b)] + I * Fx[18 * p + 2 * (3 * a + b) + 1];
+                spinor fs = colour_mul(f, 1.0, s);
+                for (int al = 0; al < 4; ++al)
+                    for (int a = 0; a < 3; ++a) {
+                        cplx acc = 0;
+                        for (int be = 0; be < 4; ++be) acc += SIGMA[mu][nu][al][be] * fs.c[be][a];
+                        r.c[al][a] += I * kappa * csw * acc;
+                    }
+            }
+        }
+        spinor_store(out, k, &r);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Conjugate gradient on the normal equations (Sec. 3.3, CG!)          */
+/* ------------------------------------------------------------------ */
+
+static double norm2(const double *v, long n)
+{
+    double s = 0;
+    for (long i = 0; i < n; ++i) s += v[i] * v[i];
+    return s;
+}
+
+/* Solves D x = b by CG on D^dag D x = D^dag b (CGNR), starting from the x
+ * passed in.  The recursion tracks r = b - D x.  When its norm falls below
+ * tol * |b| the residual is recomputed from scratch; the solve stops when
+ * that true relative residual |b - D x| / |b| is <= tol, otherwise CG is
+ * restarted from the current x.  Returns 0 on convergence, 1 if maxiter was
+ * reached; *iters is the number of D^dag D applications, *resid the last true
+ * relative residual. */
+int oracle_cgnr(const int *L, const double *U, double kappa, double csw, const double *theta,
+                const double *b, double *x, double tol, int maxiter, int *iters, double *resid)
+{
+    dirac_ctx c;
+    ctx_init(&c, L, U, kappa, csw, theta);
+    long n = 24 * volume_of(L);
+    double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * n), *w = malloc(sizeof(double) * n);
+    double bnorm = sqrt(norm2(b, n));
+    int it = 0, status = 1;
+    double rel = 0;
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+        *iters = 0;
+        *resid = 0;
+        ctx_free(&c);
+        free(r); free(z); free(p); free(w);
+        return 0;
+    }
+    for (;;) {
+        /* (re)start: r = b - D x, z = D^dag r, p = z */
+        dirac_apply(&c, x, w);
+        for (long i = 0; i < n; ++i) r[i] = b[i] - w[i];
+        rel = sqrt(norm2(r, n)) / bnorm;
+        if (rel <= tol) { status = 0; break; }
+        if (it >= maxiter) break;
+        dirac_dagger_apply(&c, r, z);
+        memcpy(p, z, sizeof(double) * n);
+        double gam = norm2(z, n);
+        while (it < maxiter) {
+            dirac_apply(&c, p, w);
+            double alpha = gam / norm2(w, n);
+            for (long i = 0; i < n; ++i) {
+                x[i] += alpha * p[i];
+                r[i] -= alpha * w[i];
+            }
+            ++it;
+            if (sqrt(norm2(r, n)) <= tol * bnorm) break;
+            dirac_dagger_apply(&c, r, z);
+            double gnew = norm2(z, n);
+            double beta = gnew / gam;
+            gam = gnew;
+            for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        }
+    }
+    *iters = it;
+    *resid = rel;
+    ctx_free(&c);
+    free(r); free(z); free(p); free(w);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Point-source propagator and pion correlator (Sec. 3.3, propagator!) */
+/* ------------------------------------------------------------------ */
+
+/* C(t) = sum_{x vec} sum_{j, alpha, a} |S_j(x vec, t)_{alpha a}|^2 from the 12
+ * columns S_j = D^{-1} eta_j, j = 3 spin + colour, prop[j][site][12] complex.
+ * t is counted from the source time slice src_t (mod T). */
+void oracle_pion_contract(const int *L, const double *prop, int src_t, double *corr)
+{
+    long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2];
+    for (int t = 0; t < L[3]; ++t) corr[t] = 0;
+    for (int j = 0; j < 12; ++j)
+        for (long s = 0; s < V; ++s) {
+            int t = (int)(s / V3);
+            int tr = ((t - src_t) % L[3] + L[3]) % L[3];
+            const double *q = prop + 24 * (V * j + s);
+            double acc = 0;
+            for (int k = 0; k < 24; ++k) acc += q[k] * q[k];
+            corr[tr] += acc;
+        }
+}
+
+/* Solves the 12 point sources at src = (x, y, z, t) and contracts them.
+ * prop (may be NULL) receives the 12 columns [j][site][12] complex; iters and
+ * resid (may be NULL) receive per-column counts and true residuals.  Returns
+ * the number of columns that did not converge. */
+int oracle_pion(const int *L, const double *U, double kappa, double csw, const double *theta,
+                const int *src, double tol, int maxiter, double *corr, double *prop, int *iters,
+                double *resid)
+{
+    long V = volume_of(L), n = 24 * V;
+    double *S = prop ? prop : malloc(sizeof(double) * 12 * n);
+    double *eta = calloc((size_t)n, sizeof(double));
+    long s0 = index_of(L, src);
+    int failed = 0;
+    for (int j = 0; j < 12; ++j) {
+        memset(eta, 0, sizeof(double) * n);
+        eta[24 * s0 + 2 * j] = 1.0;
+        double *x = S + (long)j * n;
+        memset(x, 0, sizeof(double) * n);
+        int it;
+        double res;
+        failed += oracle_cgnr(L, U, kappa, csw, theta, eta, x, tol, maxiter, &it, &res);
+        if (iters) iters[j] = it;
+        if (resid) resid[j] = res;
+    }
+    oracle_pion_contract(L, S, src[3], corr);
+    free(eta);
+    if (!prop) free(S);
+    return failed;
+}

@@ -1,0 +1,385 @@
+"""Pins for the FP64 oracle: checks against what the mathematics fixes.
+
+None of these re-types an oracle formula.  They test it against:
+  * the Clifford algebra and the chiral-basis convention (gamma matrices);
+  * the closed-form free-field (unit-link) Wilson operator and propagator in
+    momentum space, including twisted / antiperiodic boundary phases;
+  * gamma5-hermiticity and the adjoint identity on rough fields with clover;
+  * gauge covariance under a random SU(3) transformation;
+  * the clover term: zero at unit links, and the closed form on a constant
+    abelian field strength in each of the six planes (orientation, 1/8
+    normalisation, traceless projection);
+  * dense LU inversion at 2^4 and 4^4 (the solver), kappa = 0 (D = 1);
+  * translation invariance of the pion correlator (source-relative t).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_16994_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# Chiral basis, built here from the Pauli matrices (the convention the library
+# documents): g_k = [[0, -i s_k], [i s_k, 0]], g_t = [[0, -1], [-1, 0]].
+_S = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]], complex)]
+_Z = np.zeros((2, 2))
+_I2 = np.eye(2)
+BASIS = [np.block([[_Z, -1j * s], [1j * s, _Z]]) for s in _S] + [np.block([[_Z, -_I2], [-_I2, _Z]])]
+G5 = np.diag([1.0, 1.0, -1.0, -1.0]).astype(complex)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def vdot(a, b):
+    return np.vdot(a.ravel(), b.ravel())
+
+
+def g5(psi):
+    return np.einsum("ab,...bc->...ac", G5, psi)
+
+
+# --------------------------------------------------------------------------
+# gamma matrices
+# --------------------------------------------------------------------------
+
+def test_gamma_clifford_algebra_and_basis():
+    g = [oracle.gamma(mu) for mu in range(4)]
+    for mu in range(4):
+        assert np.allclose(g[mu], g[mu].conj().T, atol=0)
+        for nu in range(4):
+            assert np.allclose(g[mu] @ g[nu] + g[nu] @ g[mu], 2 * (mu == nu) * np.eye(4), atol=1e-15)
+    gamma5 = oracle.gamma(4)
+    assert np.allclose(gamma5, g[3] @ g[0] @ g[1] @ g[2], atol=1e-15)
+    assert np.allclose(gamma5, G5, atol=1e-15)
+    for mu in range(4):
+        assert np.allclose(g[mu], BASIS[mu], atol=0), mu
+
+
+# --------------------------------------------------------------------------
+# free field: closed forms in momentum space
+# --------------------------------------------------------------------------
+
+def _momenta(dims, theta):
+    """Allowed momenta p_mu = (2 pi n + phi_mu) / L_mu with theta_mu = exp(i phi_mu)."""
+    ps = []
+    for mu, L in enumerate(dims):
+        phi = np.angle(theta[mu])
+        ps.append((2 * np.pi * np.arange(L) + phi) / L)
+    return ps
+
+
+def _free_dirac_p(kappa, p):
+    """D(p) = 1 - 2 kappa sum cos p + 2 i kappa sum g_mu sin p (4x4 spin matrix)."""
+    m = (1 - 2 * kappa * sum(np.cos(pm) for pm in p)) * np.eye(4, dtype=complex)
+    for mu in range(4):
+        m = m + 2j * kappa * np.sin(p[mu]) * BASIS[mu]
+    return m
+
+
+def _coords(dims):
+    lx, ly, lz, lt = dims
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    return x, y, z, t
+
+
+@pytest.mark.parametrize("theta", [(1, 1, 1, -1), (np.exp(0.7j), np.exp(-1.1j), 1, np.exp(2.3j))])
+def test_free_dirac_on_plane_waves(theta):
+    dims = (4, 2, 6, 4)
+    kappa = 0.13
+    U = inputs.unit_gauge_field(dims)
+    ps = _momenta(dims, theta)
+    x, y, z, t = _coords(dims)
+    rng = np.random.default_rng(5)
+    for n in [(0, 0, 0, 0), (1, 1, 2, 3), (3, 0, 5, 1)]:
+        p = [ps[mu][n[mu]] for mu in range(4)]
+        phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+        u = rng.normal(size=(4, 3)) + 1j * rng.normal(size=(4, 3))
+        psi = phase[..., None, None] * u
+        want = phase[..., None, None] * (_free_dirac_p(kappa, p) @ u)
+        got = oracle.dirac(dims, U, kappa, 1.3, psi, theta=theta)
+        assert rel(got, want) < 1e-14
+
+
+def _free_propagator_x(dims, kappa, theta):
+    """S(x, 0) = V^-1 sum_p exp(i p x) S(p), S(p) = (A - 2 i kappa sum g sin p)/(A^2 + 4 kappa^2 sum sin^2).
+
+    Returns shape (T, Z, Y, X, 4, 4) (spin matrix; colour is the identity).
+    """
+    ps = _momenta(dims, theta)
+    x, y, z, t = _coords(dims)
+    V = np.prod(dims)
+    S = np.zeros(x.shape + (4, 4), dtype=complex)
+    P = np.meshgrid(*ps, indexing="ij")
+    P = [a.ravel() for a in P]
+    for k in range(len(P[0])):
+        p = [P[mu][k] for mu in range(4)]
+        A = 1 - 2 * kappa * sum(np.cos(pm) for pm in p)
+        den = A * A + 4 * kappa ** 2 * sum(np.sin(pm) ** 2 for pm in p)
+        num = A * np.eye(4, dtype=complex)
+        for mu in range(4):
+            num = num - 2j * kappa * np.sin(p[mu]) * BASIS[mu]
+        ph = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+        S += ph[..., None, None] * (num / den)
+    return S / V
+
+
+def test_free_propagator_closed_form_dense_and_cg():
+    dims = (2, 4, 2, 6)
+    kappa = 0.124
+    theta = (1, np.exp(0.4j), 1, -1)
+    U = inputs.unit_gauge_field(dims)
+    S = _free_propagator_x(dims, kappa, theta)
+    # column (spin 1, colour 2) of the solver
+    eta = inputs.point_source(dims, (0, 0, 0, 0), 1, 2)
+    x, it, res, ok = oracle.cgnr(dims, U, kappa, 0.0, eta, theta=theta, tol=1e-13)
+    assert ok and res <= 1e-13
+    want = np.zeros_like(x)
+    want[..., :, 2] = S[..., :, 1]
+    assert rel(x, want) < 1e-11
+    # dense inverse of the operator matrix agrees with the closed form everywhere
+    D = oracle.dirac_matrix(dims, U, kappa, 0.0, theta=theta)
+    Dinv = np.linalg.inv(D)
+    col = Dinv[:, 3 * 1 + 2].reshape(x.shape)
+    assert rel(col, want) < 1e-12
+
+
+def test_free_pion_correlator_closed_form():
+    dims = (4, 4, 4, 8)
+    kappa = 0.12
+    U = inputs.unit_gauge_field(dims)
+    S = _free_propagator_x(dims, kappa, (1, 1, 1, -1))
+    # C(t) = sum_xvec tr[S S^dag] with colour identity (factor 3)
+    want = 3 * np.einsum("tzyxab,tzyxab->t", S, S.conj()).real
+    corr, _, iters, res, failed = oracle.pion(dims, U, kappa, 1.0, (0, 0, 0, 0), tol=1e-13)
+    assert failed == 0 and np.all(res <= 1e-13)
+    assert rel(corr, want) < 1e-11
+    # time-reflection symmetry of the free correlator: C(t) = C(T - t)
+    assert np.allclose(corr[1:], corr[1:][::-1], rtol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# rough fields: hermiticity, adjoint, covariance
+# --------------------------------------------------------------------------
+
+ROUGH = dict(dims=(4, 2, 4, 6), eps=0.5, kappa=0.137, csw=1.7)
+
+
+def _rough():
+    d = ROUGH["dims"]
+    return d, inputs.gauge_field(d, ROUGH["eps"], seed=11)
+
+
+def test_gamma5_hermiticity_with_clover():
+    dims, U = _rough()
+    a = inputs.spinor_field(dims, seed=3)
+    b = inputs.spinor_field(dims, seed=4)
+    th = (1, np.exp(0.3j), 1, -1)
+    lhs = vdot(a, oracle.dirac(dims, U, ROUGH["kappa"], ROUGH["csw"], b, theta=th))
+    rhs = vdot(g5(oracle.dirac(dims, U, ROUGH["kappa"], ROUGH["csw"], g5(a), theta=th)), b)
+    assert abs(lhs - rhs) <= 1e-14 * abs(lhs)
+
+
+def test_adjoint_identity():
+    dims, U = _rough()
+    a = inputs.spinor_field(dims, seed=5)
+    b = inputs.spinor_field(dims, seed=6)
+    th = (np.exp(0.2j), 1, np.exp(-0.9j), -1)
+    k, c = ROUGH["kappa"], ROUGH["csw"]
+    lhs = vdot(a, oracle.dirac(dims, U, k, c, b, theta=th))
+    rhs = vdot(oracle.dirac(dims, U, k, c, a, theta=th, dagger=True), b)
+    assert abs(lhs - rhs) <= 1e-14 * abs(lhs)
+    # and the dagger equals gamma5 D gamma5 on the same field
+    assert rel(oracle.dirac(dims, U, k, c, a, theta=th, dagger=True),
+               g5(oracle.dirac(dims, U, k, c, g5(a), theta=th))) < 1e-14
+
+
+def _transform(U, g):
+    """U^g_mu(x) = g(x) U_mu(x) g(x+mu)^dag (periodic shifts)."""
+    out = np.empty_like(U)
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}
+    for mu in range(4):
+        gshift = np.roll(g, -1, axis=axis[mu])
+        out[..., mu, :, :] = g @ U[..., mu, :, :] @ np.conj(np.swapaxes(gshift, -1, -2))
+    return out
+
+
+def test_gauge_covariance():
+    dims, U = _rough()
+    g = inputs.gauge_transform(dims, seed=9)
+    psi = inputs.spinor_field(dims, seed=10)
+    k, c = ROUGH["kappa"], ROUGH["csw"]
+    Ug = _transform(U, g)
+    lhs = oracle.dirac(dims, Ug, k, c, np.einsum("...ab,...sb->...sa", g, psi))
+    rhs = np.einsum("...ab,...sb->...sa", g, oracle.dirac(dims, U, k, c, psi))
+    assert rel(lhs, rhs) < 1e-14
+    # F transforms covariantly too
+    F = oracle.field_strength(dims, U)
+    Fg = oracle.field_strength(dims, Ug)
+    gd = np.conj(np.swapaxes(g, -1, -2))
+    assert rel(Fg, g[..., None, :, :] @ F @ gd[..., None, :, :]) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# clover term
+# --------------------------------------------------------------------------
+
+def test_clover_vanishes_at_unit_links():
+    dims = (4, 4, 2, 4)
+    U = inputs.unit_gauge_field(dims)
+    psi = inputs.spinor_field(dims, seed=1)
+    assert np.abs(oracle.field_strength(dims, U)).max() == 0
+    assert rel(oracle.dirac(dims, U, 0.13, 1.9, psi), oracle.dirac(dims, U, 0.13, 0.0, psi)) == 0
+
+
+def _abelian_field(dims, mu, nu, T, n, on_nu=True):
+    """Constant field strength in the (mu, nu) plane.
+
+    on_nu: U_nu(x) = exp(i phi x_mu T) (F_{mu nu} = +phi T); otherwise
+    U_mu(x) = exp(i phi x_nu T) (F_{mu nu} = -phi T).  phi = 2 pi n / L makes
+    every plaquette, including the wrapped ones, equal to exp(+-i phi T).
+    """
+    U = inputs.unit_gauge_field(dims).copy()
+    x = _coords(dims)
+    if on_nu:
+        phi = 2 * np.pi * n / dims[mu]
+        arg = phi * x[mu]
+        U[..., nu, :, :] = 0
+        for a in range(3):
+            U[..., nu, a, a] = np.exp(1j * arg * T[a])
+    else:
+        phi = 2 * np.pi * n / dims[nu]
+        arg = phi * x[nu]
+        U[..., mu, :, :] = 0
+        for a in range(3):
+            U[..., mu, a, a] = np.exp(1j * arg * T[a])
+    return U, phi
+
+
+PLANES = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+
+
+@pytest.mark.parametrize("plane", range(6))
+@pytest.mark.parametrize("on_nu", [True, False])
+def test_clover_constant_abelian_field(plane, on_nu):
+    """D(csw) - D(0) = i kappa csw sigma_{mu nu} (x) F with F = i sin(phi) (T - tr T/3)."""
+    mu, nu = PLANES[plane]
+    dims = (4, 6, 4, 8)
+    kappa, csw = 0.125, 1.3
+    for T in [(1.0, -1.0, 0.0), (1.0, 0.0, 0.0)]:  # traceless and not: pins the projection
+        U, phi = _abelian_field(dims, mu, nu, T, n=1, on_nu=on_nu)
+        sgn = 1.0 if on_nu else -1.0
+        Fcol = 1j * sgn * np.sin(phi) * (np.diag(T) - np.trace(np.diag(T)) / 3 * np.eye(3))
+        sig = 0.5j * (BASIS[mu] @ BASIS[nu] - BASIS[nu] @ BASIS[mu])
+        psi = inputs.spinor_field(dims, seed=2)
+        got = oracle.dirac(dims, U, kappa, csw, psi) - oracle.dirac(dims, U, kappa, 0.0, psi)
+        want = 1j * kappa * csw * np.einsum("ab,cd,...bd->...ac", sig, Fcol, psi)
+        assert rel(got, want) < 1e-13, (plane, T)
+        # only that plane is populated in the stored field
+        F = oracle.field_strength(dims, U)
+        for q in range(6):
+            if q == plane:
+                assert np.allclose(F[..., q, :, :], Fcol, atol=1e-14)
+            else:
+                assert np.abs(F[..., q, :, :]).max() < 1e-14
+
+
+def test_clover_site_term_is_hermitian():
+    dims, U = _rough()
+    F = oracle.field_strength(dims, U)
+    # F is anti-Hermitian and traceless, so i sigma (x) F is Hermitian
+    assert np.abs(F + np.conj(np.swapaxes(F, -1, -2))).max() < 1e-15
+    assert np.abs(np.trace(F, axis1=-2, axis2=-1)).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# solver: dense inversion, kappa = 0
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,eps,kappa,csw", [((2, 2, 2, 2), 0.4, 0.13, 1.5), ((4, 4, 4, 4), 0.2, 0.12, 1.0)])
+def test_cgnr_matches_dense_inverse(dims, eps, kappa, csw):
+    U = inputs.gauge_field(dims, eps, seed=1)
+    b = inputs.spinor_field(dims, seed=2)
+    D = oracle.dirac_matrix(dims, U, kappa, csw)
+    xd = np.linalg.solve(D, b.ravel()).reshape(b.shape)
+    x, it, res, ok = oracle.cgnr(dims, U, kappa, csw, b, tol=1e-13)
+    assert ok and res <= 1e-13
+    assert rel(x, xd) < 1e-11
+    # the dense matrix of D^dag is the conjugate transpose of that of D
+    if dims == (2, 2, 2, 2):
+        Dd = oracle.dirac_matrix(dims, U, kappa, csw, dagger=True)
+        assert np.abs(Dd - D.conj().T).max() < 1e-15
+
+
+def test_kappa_zero_is_identity():
+    dims, U = _rough()
+    b = inputs.spinor_field(dims, seed=7)
+    assert rel(oracle.dirac(dims, U, 0.0, 1.5, b), b) == 0
+    x, it, res, ok = oracle.cgnr(dims, U, 0.0, 1.5, b)
+    assert ok and rel(x, b) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# pion correlator
+# --------------------------------------------------------------------------
+
+def test_pion_translation_invariance_and_positivity():
+    dims = (4, 4, 4, 6)
+    kappa, csw = 0.12, 1.0
+    U = inputs.gauge_field(dims, 0.3, seed=21)
+    c0, *_ = oracle.pion(dims, U, kappa, csw, (0, 0, 0, 0), tol=1e-12)
+    # shift the whole configuration by (1, 2, 3, 2) and the source with it;
+    # time shifts move across the antiperiodic boundary, which changes the
+    # propagator by a sign on some slices but leaves |S|^2 unchanged
+    shift = (1, 2, 3, 2)
+    Us = np.roll(U, shift=(shift[3], shift[2], shift[1], shift[0]), axis=(0, 1, 2, 3))
+    c1, *_ = oracle.pion(dims, Us, kappa, csw, shift, tol=1e-12)
+    assert np.all(c0 > 0)
+    assert rel(c1, c0) < 1e-10
+
+
+def test_pion_contract_sums_all_columns():
+    dims = (2, 2, 2, 4)
+    rng = np.random.default_rng(0)
+    prop = rng.normal(size=(12, 4, 2, 2, 2, 4, 3)) + 1j * rng.normal(size=(12, 4, 2, 2, 2, 4, 3))
+    corr = oracle.pion_contract(dims, prop, src_t=1)
+    # Parseval: the total over t is the squared Frobenius norm of the whole propagator
+    assert abs(corr.sum() - np.sum(np.abs(prop) ** 2)) < 1e-12 * corr.sum()
+    # a propagator living on one time slice only lands at (t - src_t) mod T
+    p1 = np.zeros_like(prop)
+    p1[:, 0] = prop[:, 0]
+    c1 = oracle.pion_contract(dims, p1, src_t=1)
+    assert np.count_nonzero(c1) == 1 and c1[3] > 0
+
+
+# --------------------------------------------------------------------------
+# the input generator (shared by both sides)
+# --------------------------------------------------------------------------
+
+def test_splitmix64_reference_outputs():
+    vals = [int(l) for l in open(os.path.join(HERE, "golden", "splitmix64_seed1234567.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = [int(v) for v in inputs.splitmix64(1234567, 0, 5)]
+    assert got == vals
+
+
+def test_gauge_generator_su3_and_mean_plaquette():
+    dims = (8, 8, 8, 8)
+    eps = 0.4
+    U = inputs.gauge_field(dims, eps, seed=3)
+    m = U.reshape(-1, 3, 3)
+    assert np.abs(m @ np.conj(np.swapaxes(m, 1, 2)) - np.eye(3)).max() < 1e-14
+    assert np.abs(np.linalg.det(m) - 1).max() < 1e-14
+    # i.i.d. adjoint-invariant links: E[Re tr P / 3] = u^4 with u = E[Re tr U / 3]
+    u = np.mean(np.trace(m, axis1=1, axis2=2).real) / 3
+    Ux, Uy = U[..., 0, :, :], U[..., 1, :, :]
+    P = Ux @ np.roll(Uy, -1, axis=3) @ np.conj(np.swapaxes(np.roll(Ux, -1, axis=2), -1, -2)) \
+        @ np.conj(np.swapaxes(Uy, -1, -2))
+    plaq = np.mean(np.trace(P, axis1=-2, axis2=-1).real) / 3
+    assert abs(plaq - u ** 4) < 0.01
+    # second-order expansion of the mean link: u = 1 - 2 eps^2 / 3 + O(eps^4)
+    assert abs(u - (1 - 2 * eps ** 2 / 3)) < 0.02
