@@ -1,0 +1,260 @@
+/*
+ * lqcd.h -- C ABI of a GB300 (sm_103a) library for the O(a)-improved Wilson
+ * (clover) point-source propagator of LatticeGPU.jl (arXiv:2503.16994).
+ *
+ * What the calls compute (the paper's Sec. 3.3, with the reading below):
+ *
+ *   (D psi)(x) = psi(x)
+ *       - kappa sum_mu [ (1 - g_mu) U~_mu(x) psi(x+mu) + (1 + g_mu) U~_mu(x-mu)^dag psi(x-mu) ]
+ *       + i kappa csw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x) psi(x)
+ *
+ *   kappa-normalised (m0 = 1/(2 kappa) - 4, D = 2 kappa Dw); U~_mu(x) carries
+ *   the boundary phase factor theta_mu on the link from x_mu = L_mu - 1 to
+ *   x_mu = 0 (theta holds full phase factors, Sec. 3.3 footnote); the default
+ *   theta = (1,1,1,-1) gives periodic space and antiperiodic time.
+ *   sigma_{mu nu} = (i/2)[g_mu, g_nu]; F_{mu nu} = (Q - Q^dag)/8 made
+ *   traceless, Q the four-leaf clover (the Csw! term of Sec. 3.3).
+ *   Gamma matrices, chiral basis, 2x2 spin blocks: g_k = [[0, -i s_k], [i s_k, 0]]
+ *   (k = x, y, z), g_t = [[0, -1], [-1, 0]], g5 = g_t g_x g_y g_z = diag(1,1,-1,-1).
+ *
+ * Host layouts (all calls): lexicographic sites, x fastest and t slowest
+ * (time is the last extent, Sec. 2.1).  Complex numbers are interleaved
+ * (re, im) doubles.
+ *   gauge field : U[t][z][y][x][mu][a][b]     (mu = 0..3 = x,y,z,t; 3x3 row-major; 72 doubles/site)
+ *   spinor field: psi[t][z][y][x][spin][colour] (24 doubles/site; component 3*spin + colour)
+ *   nrhs fields : stored one after another, field j at offset j * 24 * V doubles.
+ *
+ * Conventions:
+ *   - Every call returns LQCD_OK (0) or a negative status; it never aborts,
+ *     traps or exits.  lqcd_last_error() gives a message for the calling thread.
+ *   - The caller owns every buffer it passes.  Host pointers are read or
+ *     written only during the call.  With LQCD_DEVICE_PTRS the pointers are
+ *     device memory of the lattice's device (for example PyTorch tensors),
+ *     used in stream order on `stream`; the call returns after the work on
+ *     `stream` has completed.
+ *   - The library owns lattices, resident gauge fields (with their clover
+ *     fields) and solver workspaces; they live until the matching destroy/free.
+ *   - A lattice handle may be used from one thread at a time (calls on one
+ *     lattice are serialised internally).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LQCD_ABI_VERSION 1
+
+/* status codes */
+enum {
+    LQCD_OK = 0,
+    LQCD_EINVAL = -1,    /* bad argument (null pointer, odd extent, unknown id, ...) */
+    LQCD_ENOMEM = -2,    /* device memory or HBM budget exhausted */
+    LQCD_ECUDA = -3,     /* a CUDA call failed (message has the CUDA error string) */
+    LQCD_ENOCONV = -4,   /* a solve did not reach the tolerance within maxiter (info is filled in) */
+    LQCD_EBUSY = -5,     /* request still pending (serve poll) */
+    LQCD_ETIMEOUT = -6,  /* a bounded wait ran out (poll timeout, device-side wait cap) */
+    LQCD_ENOTFOUND = -7, /* unknown ticket */
+    LQCD_ENOTIMPL = -8   /* feature not available in this build */
+};
+
+/* solver precisions */
+enum {
+    LQCD_PREC_FP64 = 0,       /* every vector and operator in FP64 */
+    LQCD_PREC_MIXED_FP32 = 1, /* inner Krylov vectors FP32, FP32 math, recon-12 FP32 links; FP64 outer */
+    LQCD_PREC_MIXED_FP16 = 2  /* inner vectors FP16 + per-site FP32 scale, FP16 recon-12 links and
+                                 clover, FP32 math; FP64 outer */
+};
+
+/* flags for lqcd_dirac_apply / lqcd_pion_contract */
+enum {
+    LQCD_DAG = 1,         /* apply D^dag = g5 D g5 instead of D */
+    LQCD_DEVICE_PTRS = 2  /* psi_in / psi_out (or prop / corr) are device pointers */
+};
+
+typedef struct lqcd_lattice_s *lqcd_lattice; /* opaque; owns all device memory it allocates */
+typedef struct lqcd_server_s *lqcd_server;   /* opaque serving loop */
+
+/* DiracParam of Sec. 3.3 (kappa instead of m0).  theta: the four boundary
+ * phase factors (|theta_mu| = 1), re and im parts.  mu (twisted mass) must be
+ * 0 in this version. */
+typedef struct {
+    double kappa;
+    double csw;
+    double theta_re[4];
+    double theta_im[4];
+    double mu;
+} lqcd_dirac_params;
+
+/* tol: stop when the true relative residual |b - D x|_2 / |b|_2 of the full
+ * (unpreconditioned) system is <= tol.  maxiter: cap on inner iterations
+ * (applications of the normal operator) per right-hand side.  precision:
+ * LQCD_PREC_*.  inner_tol: the reliable-update factor delta (the residual is
+ * recomputed in FP64 whenever the low-precision one has dropped by delta;
+ * 0 selects the default 0.1).  nrhs: right-hand sides solved together
+ * (batched per launch), >= 1. */
+typedef struct {
+    double tol;
+    int maxiter;
+    int precision;
+    double inner_tol;
+    int nrhs;
+} lqcd_solver_params;
+
+/* Per right-hand-side result.  iters_inner: normal-operator applications;
+ * iters_outer: FP64 residual recomputations (reliable updates); true_resid:
+ * final |b - D x| / |b| computed in FP64 on the full lattice; status: LQCD_OK
+ * or LQCD_ENOCONV. */
+typedef struct {
+    int iters_inner;
+    int iters_outer;
+    double true_resid;
+    int status;
+} lqcd_solve_info;
+
+/* Thread-local message describing the last failing call of this thread. */
+const char *lqcd_last_error(void);
+
+/* LQCD_ABI_VERSION of the loaded library. */
+int lqcd_abi_version(void);
+
+/* Lattice geometry (SpaceParm of Sec. 2.1).  dims = {Lx, Ly, Lz, T}, each even
+ * and >= 2 (even-odd preconditioning needs even extents; extents of 2 are
+ * allowed, psi(x+mu) and psi(x-mu) are then the same site and both terms
+ * count).  device: CUDA ordinal.  Allocates nothing large; gauge fields and
+ * workspaces are allocated by later calls.
+ * Errors: LQCD_EINVAL (null out, odd or < 2 extent, V/2 >= 2^31),
+ * LQCD_ECUDA (bad device). */
+int lqcd_lattice_create(const int dims[4], int device, lqcd_lattice *out);
+
+/* Frees every device buffer of the lattice (gauge fields, clover fields,
+ * workspaces).  NULL is accepted. */
+int lqcd_lattice_destroy(lqcd_lattice lat);
+
+/* Makes a gauge field resident (Sec. 2.2: SU(3) links, stored on the device
+ * as FP64 and as reconstruct-12 FP32/FP16 copies keeping the first two rows;
+ * the third row is rebuilt from unitarity as conj(row0 x row1)).  U: host
+ * array in the layout above (72 doubles per site), copied; the caller keeps
+ * it.  The links must be special unitary for the recon-12 copies to be exact.
+ * *gauge_id receives an id >= 0 used by the other calls.
+ * Errors: LQCD_EINVAL, LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_gauge_upload(lqcd_lattice lat, const double *U, int *gauge_id);
+
+/* Releases a resident gauge field and its cached clover fields. */
+int lqcd_gauge_free(lqcd_lattice lat, int gauge_id);
+
+/* psi_out = D psi_in (or D^dag psi_in with LQCD_DAG), in FP64, out of place
+ * (Dw! of Sec. 3.3: both fields preallocated by the caller).  The clover
+ * field for (gauge_id, kappa, csw) is computed on first use and cached
+ * (Csw! of Sec. 3.3).  psi_in, psi_out: 24 V doubles each, host layout; host
+ * memory, or device memory with LQCD_DEVICE_PTRS.  psi_in and psi_out must
+ * not overlap.
+ * Errors: LQCD_EINVAL (null, unknown id, mu != 0), LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_dirac_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
+                     const double *psi_in, double *psi_out, int flags, void *stream);
+
+/* Solves D x_j = b_j for j = 0..nrhs-1 (CG! of Sec. 3.3) by CG on the normal
+ * equations of the even-odd preconditioned (Schur) operator
+ *   Dhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe
+ * (A = clover site term, H = hopping term), with FP64 residual recomputation
+ * (reliable updates) and an FP64 final true-residual check on the full
+ * lattice.  b, x: nrhs * 24 V doubles, host layout; host memory, or device
+ * memory when flags has LQCD_DEVICE_PTRS.  x on input is ignored (zero start).
+ * info: nrhs entries (may be NULL).  sp->nrhs is ignored; nrhs is the
+ * argument.
+ * Returns LQCD_OK when every column reached sp->tol, LQCD_ENOCONV when one
+ * did not (x and info still filled), or an error. */
+int lqcd_cg_solve(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
+                  const lqcd_solver_params *sp, const double *b, double *x, int nrhs,
+                  lqcd_solve_info *info, int flags, void *stream);
+
+/* Point-source propagator and pion correlator (propagator! of Sec. 3.3 and
+ * the contraction it enables; Sec. 4 example).  Solves the 12 columns
+ * eta_j(x) = delta_{x,src} e_j, j = 3*spin + colour, as one batch, then
+ *   corr[t] = sum_{x vec} sum_j sum_{spin,colour} |S_j(x vec, (src_t + t) mod T)|^2
+ * (t counted from the source time slice; no 1/V).  src = {x, y, z, t}.
+ * corr: T doubles (host, or device with LQCD_DEVICE_PTRS).  prop: NULL or
+ * 12 * 24 V doubles receiving the 12 columns (same memory kind as corr).
+ * info: 12 entries or NULL.  Return as lqcd_cg_solve. */
+int lqcd_pion_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
+                   const lqcd_solver_params *sp, const int src[4], double *corr, double *prop,
+                   lqcd_solve_info *info, int flags, void *stream);
+
+/* The pion contraction alone: corr[t] as above from 12 columns prop (12 * 24 V
+ * doubles, host layout) with the source on time slice src_t.  Host pointers,
+ * or device pointers with LQCD_DEVICE_PTRS.  Uses a device scratch buffer
+ * owned by the lattice. */
+int lqcd_pion_contract(lqcd_lattice lat, const double *prop, int src_t, double *corr, int flags,
+                       void *stream);
+
+/* ---------------- launch accounting and timing ------------------------- */
+
+/* Per-kernel statistics since the last lqcd_profile_reset.  launches and
+ * bytes count every launch of the kind (bytes = algorithmic bytes: each
+ * operand of the launch read or written once, all right-hand sides counted
+ * as active).  timed_*: launches bracketed by CUDA events on their stream
+ * while timing was enabled, with their summed device time.  Not part of the
+ * paper; this is the library's tracing facility (the paper times methods
+ * with TimerOutputs.jl, Sec. 3.4). */
+typedef struct {
+    char name[48];
+    long long launches;
+    double bytes;
+    long long timed_launches;
+    double timed_ms;
+    double timed_bytes;
+} lqcd_kernel_stat;
+
+/* Clears the statistics; enable_timing != 0 brackets every following launch
+ * with CUDA events (a small host overhead per launch). */
+int lqcd_profile_reset(int enable_timing);
+
+/* Copies up to max entries into out; *count receives the number of kernel
+ * kinds seen.  Waits for the timed launches to complete. */
+int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count);
+
+/* ---------------- serving loop (continuous batching) ------------------- */
+
+/* A server owns one device thread that admits propagator requests
+ * (lqcd_pion_corr work units) while HBM budget and slots allow, runs all
+ * admitted requests' iterations interleaved on the device, and retires each
+ * one independently as it converges.  hbm_budget_bytes: device memory the
+ * server may use for gauge fields and per-request workspaces (0 = 90% of
+ * free memory).  max_slots: requests resident at once (>= 1). */
+int lqcd_serve_create(int device, size_t hbm_budget_bytes, int max_slots, lqcd_server *out);
+
+/* Makes a gauge field of the given dims resident on the server (charged
+ * to the budget).  U: host, layout as lqcd_gauge_upload.  Errors as there,
+ * plus LQCD_ENOMEM when the budget cannot hold it. */
+int lqcd_serve_gauge(lqcd_server srv, const int dims[4], const double *U, int *gauge_id);
+
+/* Queues one 12-column point-source propagator + pion correlator request.
+ * Copies its arguments; non-blocking.  *ticket identifies the request.
+ * Errors: LQCD_EINVAL (unknown gauge id, bad source or params). */
+int lqcd_serve_submit(lqcd_server srv, int gauge_id, const lqcd_dirac_params *dp,
+                      const lqcd_solver_params *sp, const int src[4], uint64_t *ticket);
+
+/* Waits up to timeout_ms (0 = just look, < 0 = forever) for a request.
+ * On completion fills corr (T doubles), info (12 entries) and timestamps
+ * {arrive, admit, start, finish} (seconds on a monotonic clock; any of the
+ * three pointers may be NULL) and forgets the ticket.  Returns LQCD_OK when
+ * done, LQCD_ENOCONV when done but a column did not converge, LQCD_EBUSY when
+ * still queued or running and timeout_ms == 0, LQCD_ETIMEOUT when the wait
+ * ran out, LQCD_ENOTFOUND for an unknown ticket, or the request's error. */
+int lqcd_serve_poll(lqcd_server srv, uint64_t ticket, double *corr, lqcd_solve_info *info,
+                    double timestamps[4], int timeout_ms);
+
+/* Stops the device thread; requests not finished yet are cancelled and
+ * their tickets forgotten.  Frees everything.  NULL is accepted. */
+int lqcd_serve_destroy(lqcd_server srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

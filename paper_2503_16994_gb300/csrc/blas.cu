@@ -1,0 +1,89 @@
+// Launchers of the CG vector kernels (explicit instantiations).
+#include "lqcd_impl.h"
+
+namespace lqcd {
+
+// |x|^2 of an FP64 field -> red.op
+__global__ void __launch_bounds__(128) norm2_f64(VecArgs v, SpinorField<F64> x)
+{
+    const int j = blockIdx.x % v.nrhs, tile = blockIdx.x / v.nrhs;
+    if (v.gate_st && v.gate_st[j].status != v.gate) return;
+    const int i = tile * blockDim.x + threadIdx.x;
+    double n2 = 0.0;
+    if (i < v.vh) n2 = norm2_sp(load_spinor<F64, double>(x, j, i));
+    reduce_finish(v.red, j, tile, v.ntiles, n2);
+}
+
+static unsigned grid_of(const VecArgs &v) { return unsigned(v.ntiles * v.nrhs); }
+
+template <class W, class E>
+void launch_er_update(const VecArgs &v, SpinorField<W> p, SpinorField<W> w, SpinorField<W> r, SpinorField<E> e,
+                      cudaStream_t st)
+{
+    ProfScope prof(prec_name<W>() == std::string("f64") ? "cg_er_update_f64" : (prec_name<W>() == std::string("f32") ? "cg_er_update_f32" : "cg_er_update_f16"),
+                   double(v.vh) * v.nrhs * (4.0 * spinor_bytes<W>() + 2.0 * spinor_bytes<E>()), st);
+    cg_er_update<W, E><<<grid_of(v), kBlock, 0, st>>>(v, p, w, r, e);
+    LQCD_CHECK_LAUNCH();
+}
+
+template <class W>
+void launch_p_update(const VecArgs &v, const RhsState *s, SpinorField<W> z, SpinorField<W> p, cudaStream_t st)
+{
+    ProfScope prof("cg_p_update", double(v.vh) * v.nrhs * 3.0 * spinor_bytes<W>(), st);
+    cg_p_update<W><<<grid_of(v), kBlock, 0, st>>>(v, s, z, p);
+    LQCD_CHECK_LAUNCH();
+}
+
+template <class E>
+void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, SpinorField<F64> x, cudaStream_t st)
+{
+    ProfScope prof("cg_x_update", double(v.vh) * v.nrhs * (2.0 * spinor_bytes<E>() + 2.0 * 192.0), st);
+    cg_x_update<E><<<grid_of(v), kBlock, 0, st>>>(v, s, e, x);
+    LQCD_CHECK_LAUNCH();
+}
+
+template <class W>
+void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> w, SpinorField<W> r, cudaStream_t st)
+{
+    ProfScope prof("cg_r_replace", double(v.vh) * v.nrhs * (2.0 * 192.0 + spinor_bytes<W>()), st);
+    cg_r_replace<W><<<grid_of(v), kBlock, 0, st>>>(v, bhat, w, r);
+    LQCD_CHECK_LAUNCH();
+}
+
+void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st)
+{
+    ProfScope prof("norm2_f64", double(v.vh) * v.nrhs * 192.0, st);
+    norm2_f64<<<grid_of(v), kBlock, 0, st>>>(v, x);
+    LQCD_CHECK_LAUNCH();
+}
+
+template <class S, class C>
+void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
+                         cudaStream_t st)
+{
+    ProfScope prof("clover_apply", double(vh) * (nrhs * 2.0 * spinor_bytes<S>() + clover_bytes<C>()), st);
+    clover_apply_kernel<S, C><<<unsigned(ntiles_of(vh) * nrhs), kBlock, 0, st>>>(int(vh), nrhs, parity, cl, in, out);
+    LQCD_CHECK_LAUNCH();
+}
+
+template void launch_er_update<F64, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F64>,
+                                         SpinorField<F64>, cudaStream_t);
+template void launch_er_update<F32, F32>(const VecArgs &, SpinorField<F32>, SpinorField<F32>, SpinorField<F32>,
+                                         SpinorField<F32>, cudaStream_t);
+template void launch_er_update<F16, F32>(const VecArgs &, SpinorField<F16>, SpinorField<F16>, SpinorField<F16>,
+                                         SpinorField<F32>, cudaStream_t);
+template void launch_p_update<F64>(const VecArgs &, const RhsState *, SpinorField<F64>, SpinorField<F64>, cudaStream_t);
+template void launch_p_update<F32>(const VecArgs &, const RhsState *, SpinorField<F32>, SpinorField<F32>, cudaStream_t);
+template void launch_p_update<F16>(const VecArgs &, const RhsState *, SpinorField<F16>, SpinorField<F16>, cudaStream_t);
+template void launch_x_update<F64>(const VecArgs &, const RhsState *, SpinorField<F64>, SpinorField<F64>, cudaStream_t);
+template void launch_x_update<F32>(const VecArgs &, const RhsState *, SpinorField<F32>, SpinorField<F64>, cudaStream_t);
+template void launch_r_replace<F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F64>,
+                                    cudaStream_t);
+template void launch_r_replace<F32>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F32>,
+                                    cudaStream_t);
+template void launch_r_replace<F16>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F16>,
+                                    cudaStream_t);
+template void launch_clover_apply<F64, F64>(long, int, int, CloverField<F64>, SpinorField<F64>, SpinorField<F64>,
+                                            cudaStream_t);
+
+}  // namespace lqcd

@@ -1,0 +1,185 @@
+// Host-side internals of the library: lattice handle, resident gauge and
+// clover fields, solver workspaces, kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/lqcd.h"
+#include "kernels.cuh"
+
+namespace lqcd {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define LQCD_CUDA(call)                                                                             \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            throw ::lqcd::Error{e_ == cudaErrorMemoryAllocation ? LQCD_ENOMEM : LQCD_ECUDA,         \
+                                std::string(#call) + ": " + cudaGetErrorString(e_)};                \
+    } while (0)
+
+#define LQCD_CHECK_LAUNCH() LQCD_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device memory owned by the library
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (re)allocates when smaller than `n` bytes; contents are not kept
+    void ensure(size_t n)
+    {
+        if (bytes >= n) return;
+        release();
+        LQCD_CUDA(cudaMalloc(&p, n));
+        bytes = n;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// resident fields
+// ---------------------------------------------------------------------------
+struct CloverSet {
+    DevBuf a64, ainv64;  // [parity][36 double2 planes]
+    DevBuf a32, ainv32;  // [parity][18 float4 planes]
+    DevBuf a16, ainv16;  // [parity][9 uint4 planes]
+};
+
+struct GaugeSet {
+    DevBuf u64;             // [parity][mu][9 double2 planes]
+    DevBuf u32;             // [parity][mu][3 float4 planes]
+    DevBuf u16, u16b;       // [parity][mu] uint4 plane + uint2 plane
+    std::map<double, std::unique_ptr<CloverSet>> clover;  // keyed by kappa * csw
+};
+
+// Storage-format-specific field pointers for one (gauge, clover) pair.
+template <class S> LinkField<S> link_field(const GaugeSet &g, long stride);
+template <class S> CloverField<S> clover_field(const CloverSet &c, bool inverse, long stride);
+
+// Solver workspace for one (nrhs, precision): fields of one parity each.
+struct Workspace {
+    int nrhs = 0, prec = -1;
+    DevBuf b_e, b_o, bhat, x_e, x_o, t64, w64;   // FP64
+    DevBuf p, t, w, r, z;                        // inner precision
+    DevBuf p_sc, t_sc, w_sc, r_sc, z_sc;         // FP16 scales
+    DevBuf e;                                    // correction (FP32, or FP64 for the FP64 solver)
+    DevBuf state;                                // RhsState[nrhs]
+    DevBuf partial, counter;                     // reductions
+    RhsState *host_state = nullptr;              // pinned mirror
+    ~Workspace();
+};
+
+}  // namespace lqcd
+
+struct lqcd_lattice_s {
+    int dims[4];
+    int device;
+    long V, vh, stride;
+    lqcd::Geom geom;
+    std::mutex mu;
+    std::map<int, std::unique_ptr<lqcd::GaugeSet>> gauges;
+    int next_gauge = 0;
+    std::map<std::pair<int, int>, std::unique_ptr<lqcd::Workspace>> ws;  // keyed by (nrhs, precision)
+    lqcd::DevBuf staging;         // host-layout fields on the device
+    lqcd::DevBuf staging2;
+    lqcd::DevBuf red_partial, red_counter, red_state;  // reductions outside the solver
+};
+
+namespace lqcd {
+
+constexpr int kBlock = 128;
+
+// Counts (and, when enabled, times) one kernel launch made in its lifetime.
+struct ProfScope {
+    std::string name;
+    double bytes;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool timed = false;
+    ProfScope(const char *name, double bytes, cudaStream_t st);
+    ~ProfScope();
+};
+
+// algorithmic bytes per site of one field in a storage format
+template <class S> constexpr double spinor_bytes() { return S::W == 2 ? 192.0 : (S::W == 4 ? 96.0 : 52.0); }
+template <class S> constexpr double link_bytes() { return S::W == 2 ? 144.0 : (S::W == 4 ? 48.0 : 24.0); }
+template <class S> constexpr double clover_bytes() { return S::W == 2 ? 576.0 : (S::W == 4 ? 288.0 : 144.0); }
+template <class S> constexpr const char *prec_name() { return S::W == 2 ? "f64" : (S::W == 4 ? "f32" : "f16"); }
+
+inline int ntiles_of(long vh) { return int((vh + kBlock - 1) / kBlock); }
+
+// gauge / clover setup (field_ops.cu)
+void gauge_repack(lqcd_lattice_s *lat, GaugeSet &g, const double *U_dev_aos, cudaStream_t st);
+CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st);
+
+// host-layout <-> even-odd SoA FP64 (field_ops.cu)
+void spinor_to_soa(lqcd_lattice_s *lat, const double *aos, int nrhs, SpinorField<F64> even, SpinorField<F64> odd,
+                   cudaStream_t st);
+void spinor_from_soa(lqcd_lattice_s *lat, double *aos, int nrhs, SpinorField<F64> even, SpinorField<F64> odd,
+                     cudaStream_t st);
+void point_sources(lqcd_lattice_s *lat, const int src[4], SpinorField<F64> even, SpinorField<F64> odd,
+                   cudaStream_t st);
+// corr[t] (device, T doubles) from 12 FP64 SoA columns, t relative to src_t
+void pion_contract_soa(lqcd_lattice_s *lat, SpinorField<F64> even, SpinorField<F64> odd, int src_t,
+                       double *corr_dev, cudaStream_t st);
+// corr[t] from 12 host-layout columns already on the device
+void pion_contract_aos(lqcd_lattice_s *lat, const double *prop_dev, int src_t, double *corr_dev,
+                       double *partial, unsigned *counter, cudaStream_t st);
+
+// hopping kernels (dslash_f64.cu, dslash_f32.cu, dslash_f16.cu)
+template <class S, class L, class C>
+void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaStream_t st);
+
+// vector kernels (blas_*.cu)
+template <class W, class E>
+void launch_er_update(const VecArgs &v, SpinorField<W> p, SpinorField<W> w, SpinorField<W> r, SpinorField<E> e,
+                      cudaStream_t st);
+template <class W>
+void launch_p_update(const VecArgs &v, const RhsState *s, SpinorField<W> z, SpinorField<W> p, cudaStream_t st);
+template <class E>
+void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, SpinorField<F64> x, cudaStream_t st);
+template <class W>
+void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> w, SpinorField<W> r,
+                      cudaStream_t st);
+void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st);
+template <class S, class C>
+void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
+                         cudaStream_t st);
+
+// solver (solver.cu)
+void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
+                     bool dag, cudaStream_t st);
+int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,
+          const double *b_dev, double *x_dev, const int *src, int nrhs, lqcd_solve_info *info, double *corr_dev,
+          cudaStream_t st);
+
+}  // namespace lqcd

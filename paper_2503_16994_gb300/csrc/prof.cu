@@ -1,0 +1,129 @@
+// Kernel launch accounting: every launch is counted per kernel kind with its
+// algorithmic bytes (each operand touched once); when timing is enabled a
+// pair of CUDA events brackets each launch on its own stream and the elapsed
+// times are summed when the statistics are read.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "lqcd_impl.h"
+
+namespace lqcd {
+
+namespace {
+struct Stat {
+    long long launches = 0;
+    double ms = 0.0, bytes = 0.0, timed_bytes = 0.0;
+    long long timed = 0;
+};
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+    double bytes;
+};
+std::mutex g_mu;
+std::map<std::string, Stat> g_stats;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_pool;
+bool g_timing = false;
+
+cudaEvent_t get_event()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    LQCD_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void drain_locked()
+{
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            Stat &s = g_stats[p.name];
+            s.ms += ms;
+            s.timed += 1;
+            s.timed_bytes += p.bytes;
+        }
+        g_pool.push_back(p.a);
+        g_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+}  // namespace
+
+ProfScope::ProfScope(const char *name_, double bytes_, cudaStream_t st_) : name(name_), bytes(bytes_), st(st_)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    Stat &s = g_stats[name];
+    s.launches += 1;
+    s.bytes += bytes;
+    if (g_timing) {
+        a = get_event();
+        b = get_event();
+        LQCD_CUDA(cudaEventRecord(a, st));
+        timed = true;
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (!timed) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (cudaEventRecord(b, st) == cudaSuccess) {
+        g_pending.push_back({name, a, b, bytes});
+        if (g_pending.size() > 100000) drain_locked();
+    }
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+int lqcd_profile_reset(int enable_timing)
+{
+    try {
+        std::lock_guard<std::mutex> lk(g_mu);
+        drain_locked();
+        g_stats.clear();
+        g_timing = enable_timing != 0;
+        return LQCD_OK;
+    } catch (const Error &e) {
+        return fail(e.code, e.msg);
+    }
+}
+
+int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count)
+{
+    if (!count || (max > 0 && !out)) return fail(LQCD_EINVAL, "null argument");
+    try {
+        std::lock_guard<std::mutex> lk(g_mu);
+        drain_locked();
+        int n = 0;
+        for (auto &kv : g_stats) {
+            if (n < max) {
+                lqcd_kernel_stat &o = out[n];
+                std::memset(&o, 0, sizeof o);
+                std::strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
+                o.launches = kv.second.launches;
+                o.bytes = kv.second.bytes;
+                o.timed_launches = kv.second.timed;
+                o.timed_ms = kv.second.ms;
+                o.timed_bytes = kv.second.timed_bytes;
+            }
+            ++n;
+        }
+        *count = n;
+        return LQCD_OK;
+    } catch (const Error &e) {
+        return fail(e.code, e.msg);
+    }
+}
+
+}  // extern "C"

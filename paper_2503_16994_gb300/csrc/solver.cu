@@ -1,0 +1,426 @@
+// Even-odd preconditioned CG (CGLS form) with FP64 reliable updates.
+//
+// System: D x = b with D = [[A_ee, -k H_eo], [-k H_oe, A_oo]] (A = clover site
+// term, H = hopping term, k = kappa).  Schur complement on the even sites:
+//   Dhat = A_ee - k^2 H_eo A_oo^-1 H_oe,  bhat = b_e + k H_eo A_oo^-1 b_o,
+//   x_o  = A_oo^-1 (b_o + k H_oe x_e),
+// and the full residual equals bhat - Dhat x_e on the even sites (zero on the
+// odd ones), so |b - D x| = |bhat - Dhat x_e| up to rounding.
+//
+// Dhat is solved by CG on the normal equations in CGLS form (the recursion
+// tracks r = rhat - Dhat e, the residual of the system itself):
+//   z = Dhat^dag r, p = z, gamma = |z|^2
+//   repeat: w = Dhat p; alpha = gamma/|w|^2; e += alpha p; r -= alpha w;
+//           z = Dhat^dag r; beta = |z|^2/gamma; gamma = |z|^2; p = z + beta p
+// with Dhat^dag = g5 Dhat g5 (the hopping projectors swap, the clover term
+// commutes with g5).  The inner vectors are FP64, FP32 or FP16; every time the
+// inner residual has dropped by delta (or looks converged, or the iteration
+// cap is hit) the correction is added to the FP64 solution and the residual
+// is recomputed in FP64 (reliable update), keeping p.  Per-RHS scalars and
+// the state machine live on the device; the host only polls the states every
+// few iterations.
+#include <algorithm>
+#include <cmath>
+
+#include "lqcd_impl.h"
+
+namespace lqcd {
+
+template <class S> static size_t field_bytes(long stride, int nrhs)
+{
+    return sizeof(typename S::word) * spinor_planes<S>::n * (size_t)stride * nrhs;
+}
+
+template <class S> static SpinorField<S> fld(DevBuf &b, DevBuf *sc, long stride)
+{
+    return {b.as<typename S::word>(), sc ? sc->as<float>() : nullptr, stride};
+}
+
+Workspace::~Workspace()
+{
+    if (host_state) cudaFreeHost(host_state);
+}
+
+template <class W, class E>
+static Workspace &workspace(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_t st)
+{
+    auto key = std::make_pair(nrhs, prec);
+    auto it = lat->ws.find(key);
+    if (it != lat->ws.end()) return *it->second;
+    auto w = std::make_unique<Workspace>();
+    w->nrhs = nrhs;
+    w->prec = prec;
+    const long S = lat->stride;
+    for (DevBuf *b : {&w->b_e, &w->b_o, &w->bhat, &w->x_e, &w->x_o, &w->t64, &w->w64}) b->ensure(field_bytes<F64>(S, nrhs));
+    for (DevBuf *b : {&w->p, &w->t, &w->w, &w->r, &w->z}) b->ensure(field_bytes<W>(S, nrhs));
+    if (std::is_same<W, F16>::value)
+        for (DevBuf *b : {&w->p_sc, &w->t_sc, &w->w_sc, &w->r_sc, &w->z_sc}) b->ensure(sizeof(float) * S * nrhs);
+    w->e.ensure(field_bytes<E>(S, nrhs));
+    w->state.ensure(sizeof(RhsState) * nrhs);
+    w->partial.ensure(sizeof(double) * (size_t)nrhs * ntiles_of(lat->vh));
+    w->counter.ensure(sizeof(unsigned) * nrhs);
+    LQCD_CUDA(cudaMemsetAsync(w->counter.p, 0, w->counter.bytes, st));
+    LQCD_CUDA(cudaMallocHost(&w->host_state, sizeof(RhsState) * nrhs));
+    Workspace &ref = *w;
+    lat->ws.emplace(key, std::move(w));
+    return ref;
+}
+
+__global__ void init_state_kernel(RhsState *s, int nrhs, double tol2, double delta2, int maxiter)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nrhs) return;
+    RhsState q = s[j];
+    q.bnorm2 = q.acc;
+    q.scale = q.bnorm2 > 0.0 ? sqrt(q.bnorm2) : 1.0;
+    q.target2 = tol2 * q.bnorm2;
+    q.delta2 = delta2;
+    q.maxiter = maxiter;
+    q.status = q.bnorm2 > 0.0 ? ST_UPDATE : ST_DONE;
+    q.gamma = q.alpha = q.beta = 0.0;
+    q.rr = q.rr_ref = 0.0;
+    q.iter = 0;
+    q.updates = -1;  // the first FP64 residual (of the zero start) is not an update
+    s[j] = q;
+}
+
+template <class W, class E>
+struct Solver {
+    lqcd_lattice_s *lat;
+    Workspace &ws;
+    int nrhs;
+    double kappa;
+    cudaStream_t st;
+    HopArgs<F64, F64, F64> h64;
+    HopArgs<W, W, W> hw;
+    CloverField<F64> a64, ai64;
+    CloverField<W> aw, aiw;
+    SpinorField<F64> b_e, b_o, bhat, x_e, x_o, t64, w64;
+    SpinorField<W> p, t, w, r, z;
+    SpinorField<E> e;
+    RhsState *S;
+    VecArgs v;
+
+    Solver(lqcd_lattice_s *l, Workspace &w_, GaugeSet &g, CloverSet &cl, const lqcd_dirac_params &dp, int n,
+           cudaStream_t s)
+        : lat(l), ws(w_), nrhs(n), kappa(dp.kappa), st(s)
+    {
+        const long Sd = lat->stride;
+        b_e = fld<F64>(ws.b_e, nullptr, Sd);
+        b_o = fld<F64>(ws.b_o, nullptr, Sd);
+        bhat = fld<F64>(ws.bhat, nullptr, Sd);
+        x_e = fld<F64>(ws.x_e, nullptr, Sd);
+        x_o = fld<F64>(ws.x_o, nullptr, Sd);
+        t64 = fld<F64>(ws.t64, nullptr, Sd);
+        w64 = fld<F64>(ws.w64, nullptr, Sd);
+        const bool h = std::is_same<W, F16>::value;
+        p = fld<W>(ws.p, h ? &ws.p_sc : nullptr, Sd);
+        t = fld<W>(ws.t, h ? &ws.t_sc : nullptr, Sd);
+        w = fld<W>(ws.w, h ? &ws.w_sc : nullptr, Sd);
+        r = fld<W>(ws.r, h ? &ws.r_sc : nullptr, Sd);
+        z = fld<W>(ws.z, h ? &ws.z_sc : nullptr, Sd);
+        e = fld<E>(ws.e, nullptr, Sd);
+        S = ws.state.as<RhsState>();
+        a64 = clover_field<F64>(cl, false, Sd);
+        ai64 = clover_field<F64>(cl, true, Sd);
+        aw = clover_field<W>(cl, false, Sd);
+        aiw = clover_field<W>(cl, true, Sd);
+        const int nt = ntiles_of(lat->vh);
+        Reduce red{ws.partial.as<double>(), ws.counter.as<unsigned>(), S, RED_STORE};
+        v = VecArgs{int(lat->vh), nrhs, nt, nullptr, 0, red};
+        h64 = HopArgs<F64, F64, F64>{};
+        h64.g = lat->geom;
+        h64.nrhs = nrhs;
+        h64.ntiles = nt;
+        h64.U = link_field<F64>(g, Sd);
+        for (int mu = 0; mu < 4; ++mu) {
+            h64.th_re[mu] = dp.theta_re[mu];
+            h64.th_im[mu] = dp.theta_im[mu];
+        }
+        h64.red = red;
+        hw = HopArgs<W, W, W>{};
+        hw.g = lat->geom;
+        hw.nrhs = nrhs;
+        hw.ntiles = nt;
+        hw.U = link_field<W>(g, Sd);
+        for (int mu = 0; mu < 4; ++mu) {
+            hw.th_re[mu] = dp.theta_re[mu];
+            hw.th_im[mu] = dp.theta_im[mu];
+        }
+        hw.red = red;
+    }
+
+    VecArgs gated(int gate, int op) const
+    {
+        VecArgs q = v;
+        q.gate_st = S;
+        q.gate = gate;
+        q.red.op = op;
+        return q;
+    }
+
+    // |b|^2, bhat = b_e + k H_eo A_oo^-1 b_o, state initialisation, x = e = p = 0
+    void prepare(double tol_eff, double delta, int maxiter)
+    {
+        VecArgs q = v;
+        q.red.op = RED_STORE;
+        launch_norm2_f64(q, b_e, st);
+        q.red.op = RED_ADD;
+        launch_norm2_f64(q, b_o, st);
+        launch_clover_apply<F64, F64>(lat->vh, nrhs, 1, ai64, b_o, t64, st);
+        HopArgs<F64, F64, F64> a = h64;
+        a.parity = 0;
+        a.in = t64;
+        a.self = b_e;
+        a.out = bhat;
+        a.coef = kappa;
+        launch_hop(a, SELF_PLAIN, false, false, st);
+        init_state_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(S, nrhs, tol_eff * tol_eff, delta * delta, maxiter);
+        LQCD_CHECK_LAUNCH();
+        LQCD_CUDA(cudaMemsetAsync(ws.x_e.p, 0, ws.x_e.bytes, st));
+        LQCD_CUDA(cudaMemsetAsync(ws.e.p, 0, ws.e.bytes, st));
+        LQCD_CUDA(cudaMemsetAsync(ws.p.p, 0, ws.p.bytes, st));
+        if (ws.p_sc.p) LQCD_CUDA(cudaMemsetAsync(ws.p_sc.p, 0, ws.p_sc.bytes, st));
+    }
+
+    // x += scale e; rhat = bhat - Dhat x (FP64); r = rhat / scale   [gate UPDATE]
+    void reliable_update()
+    {
+        launch_x_update<E>(gated(ST_UPDATE, RED_STORE), S, e, x_e, st);
+        HopArgs<F64, F64, F64> a = h64;
+        a.gate_st = S;
+        a.gate = ST_UPDATE;
+        a.parity = 1;
+        a.in = x_e;
+        a.out = t64;
+        a.clov = ai64;
+        a.coef = kappa;
+        launch_hop(a, HOP_CLOV, false, false, st);
+        a.parity = 0;
+        a.in = t64;
+        a.self = x_e;
+        a.out = w64;
+        a.clov = a64;
+        a.coef = -kappa;
+        launch_hop(a, SELF_CLOV, false, false, st);
+        launch_r_replace<W>(gated(ST_UPDATE, RED_RHAT), bhat, w64, r, st);
+    }
+
+    // w = Dhat p (|w|^2 -> alpha); e += alpha p; r -= alpha w   [gate ACTIVE]
+    void half1()
+    {
+        HopArgs<W, W, W> a = hw;
+        a.gate_st = S;
+        a.gate = ST_ACTIVE;
+        a.parity = 1;
+        a.in = p;
+        a.out = t;
+        a.clov = aiw;
+        a.coef = kappa;
+        launch_hop(a, HOP_CLOV, false, false, st);
+        a.parity = 0;
+        a.in = t;
+        a.self = p;
+        a.out = w;
+        a.clov = aw;
+        a.coef = -kappa;
+        a.red.op = RED_ALPHA;
+        launch_hop(a, SELF_CLOV, false, true, st);
+        launch_er_update<W, E>(gated(ST_ACTIVE, RED_RUPDATE), p, w, r, e, st);
+    }
+
+    // z = Dhat^dag r (|z|^2 -> beta, gamma); p = z + beta p   [gate ACTIVE]
+    void half2()
+    {
+        HopArgs<W, W, W> a = hw;
+        a.gate_st = S;
+        a.gate = ST_ACTIVE;
+        a.parity = 1;
+        a.in = r;
+        a.out = t;
+        a.clov = aiw;
+        a.coef = kappa;
+        launch_hop(a, HOP_CLOV, true, false, st);
+        a.parity = 0;
+        a.in = t;
+        a.self = r;
+        a.out = z;
+        a.clov = aw;
+        a.coef = -kappa;
+        a.red.op = RED_BETA;
+        launch_hop(a, SELF_CLOV, true, true, st);
+        launch_p_update<W>(gated(ST_ACTIVE, RED_STORE), S, z, p, st);
+    }
+
+    // x_o = A_oo^-1 (b_o + k H_oe x_e); acc = |b - D x|^2 over both parities
+    void finish()
+    {
+        HopArgs<F64, F64, F64> a = h64;
+        a.parity = 1;
+        a.in = x_e;
+        a.self = b_o;
+        a.out = x_o;
+        a.clov = ai64;
+        a.coef = kappa;
+        launch_hop(a, CLOV_SUM, false, false, st);
+        a.parity = 0;
+        a.in = x_o;
+        a.self = x_e;
+        a.b = b_e;
+        a.clov = a64;
+        a.coef = -kappa;
+        a.red.op = RED_STORE;
+        launch_hop(a, RESID, false, true, st);
+        a.parity = 1;
+        a.in = x_e;
+        a.self = x_o;
+        a.b = b_o;
+        a.red.op = RED_ADD;
+        launch_hop(a, RESID, false, true, st);
+    }
+
+    void pull_states()
+    {
+        LQCD_CUDA(cudaMemcpyAsync(ws.host_state, S, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, st));
+        LQCD_CUDA(cudaStreamSynchronize(st));
+    }
+
+    void push_states()
+    {
+        LQCD_CUDA(cudaMemcpyAsync(S, ws.host_state, sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, st));
+    }
+
+    bool all_finished() const
+    {
+        for (int j = 0; j < nrhs; ++j) {
+            int s = ws.host_state[j].status;
+            if (s == ST_ACTIVE || s == ST_UPDATE) return false;
+        }
+        return true;
+    }
+
+    // returns the number of RHS that did not reach tol
+    int run(const lqcd_solver_params &sp, lqcd_solve_info *info)
+    {
+        const double delta = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : 0.1);
+        const double tol = sp.tol;
+        prepare(0.5 * tol, delta, sp.maxiter);
+        reliable_update();
+        half2();
+        const int chunk = 8;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            long guard = (long)sp.maxiter + 64;
+            for (long it = 0; it < guard; it += chunk) {
+                for (int k = 0; k < chunk; ++k) {
+                    half1();
+                    reliable_update();
+                    half2();
+                }
+                pull_states();
+                if (all_finished()) break;
+            }
+            finish();
+            pull_states();
+            bool retry = false;
+            for (int j = 0; j < nrhs; ++j) {
+                RhsState &q = ws.host_state[j];
+                double tr = q.bnorm2 > 0 ? std::sqrt(q.acc / q.bnorm2) : 0.0;
+                if (q.status == ST_DONE && tr > tol && q.iter < q.maxiter) {
+                    q.target2 *= 0.25 * std::min(1.0, tol * tol * q.bnorm2 / std::max(q.acc, 1e-300));
+                    q.status = ST_UPDATE;
+                    retry = true;
+                }
+            }
+            if (!retry) break;
+            push_states();
+            reliable_update();
+            half2();
+        }
+        int failed = 0;
+        for (int j = 0; j < nrhs; ++j) {
+            const RhsState &q = ws.host_state[j];
+            double tr = q.bnorm2 > 0 ? std::sqrt(q.acc / q.bnorm2) : 0.0;
+            bool ok = (q.status == ST_DONE) && tr <= tol;
+            if (!ok) ++failed;
+            if (info) {
+                info[j].iters_inner = q.iter;
+                info[j].iters_outer = std::max(q.updates, 0);
+                info[j].true_resid = tr;
+                info[j].status = ok ? LQCD_OK : LQCD_ENOCONV;
+            }
+        }
+        return failed;
+    }
+};
+
+template <class W, class E>
+static int solve_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, const lqcd_dirac_params &dp,
+                      const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
+                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st)
+{
+    Workspace &ws = workspace<W, E>(lat, nrhs, sp.precision, st);
+    Solver<W, E> s(lat, ws, g, cl, dp, nrhs, st);
+    if (src)
+        point_sources(lat, src, s.b_e, s.b_o, st);
+    else
+        spinor_to_soa(lat, b_dev, nrhs, s.b_e, s.b_o, st);
+    int failed = s.run(sp, info);
+    if (x_dev) spinor_from_soa(lat, x_dev, nrhs, s.x_e, s.x_o, st);
+    if (corr_dev) pion_contract_soa(lat, s.x_e, s.x_o, src[3], corr_dev, st);
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    return failed;
+}
+
+void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
+                     bool dag, cudaStream_t st)
+{
+    CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
+    Workspace &ws = workspace<F64, F64>(lat, 1, LQCD_PREC_FP64, st);
+    const long Sd = lat->stride;
+    SpinorField<F64> ie = fld<F64>(ws.b_e, nullptr, Sd), io = fld<F64>(ws.b_o, nullptr, Sd);
+    SpinorField<F64> oe = fld<F64>(ws.x_e, nullptr, Sd), oo = fld<F64>(ws.x_o, nullptr, Sd);
+    spinor_to_soa(lat, in, 1, ie, io, st);
+    HopArgs<F64, F64, F64> a{};
+    a.g = lat->geom;
+    a.nrhs = 1;
+    a.ntiles = ntiles_of(lat->vh);
+    a.U = link_field<F64>(g, Sd);
+    for (int mu = 0; mu < 4; ++mu) {
+        a.th_re[mu] = dp.theta_re[mu];
+        a.th_im[mu] = dp.theta_im[mu];
+    }
+    a.clov = clover_field<F64>(cl, false, Sd);
+    a.coef = -dp.kappa;
+    // (D psi)_p = A_p psi_p - kappa H_{p,1-p} psi_{1-p} on both parities
+    a.parity = 0;
+    a.in = io;
+    a.self = ie;
+    a.out = oe;
+    launch_hop(a, SELF_CLOV, dag, false, st);
+    a.parity = 1;
+    a.in = ie;
+    a.self = io;
+    a.out = oo;
+    launch_hop(a, SELF_CLOV, dag, false, st);
+    spinor_from_soa(lat, out, 1, oe, oo, st);
+}
+
+int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,
+          const double *b_dev, double *x_dev, const int *src, int nrhs, lqcd_solve_info *info, double *corr_dev,
+          cudaStream_t st)
+{
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) throw Error{LQCD_EINVAL, "unknown gauge id"};
+    GaugeSet &g = *it->second;
+    CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
+    switch (sp.precision) {
+    case LQCD_PREC_FP64: return solve_prec<F64, F64>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+    case LQCD_PREC_MIXED_FP32:
+        return solve_prec<F32, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+    case LQCD_PREC_MIXED_FP16:
+        return solve_prec<F16, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+    default: throw Error{LQCD_EINVAL, "unknown precision"};
+    }
+}
+
+}  // namespace lqcd

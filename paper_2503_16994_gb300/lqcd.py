@@ -1,0 +1,344 @@
+"""Python binding of the C ABI in include/lqcd.h (ctypes; marshalling only).
+
+The names follow the C calls without the ``lqcd_`` prefix.  Every step of
+the computation runs in liblqcd.so; there is no Python or CPU fallback: if
+the library is not built, importing works but every call raises
+``LqcdError`` with the build instructions.
+
+Fields are numpy ``complex128`` arrays in the host layout of lqcd.h
+(``U[t,z,y,x,mu,3,3]``, ``psi[..., t,z,y,x,spin,colour]``) or CUDA tensors
+(PyTorch, complex128 or float64 with the same number of reals), which are
+passed as device pointers together with the tensor's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBUSY, ETIMEOUT, ENOTFOUND, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6, -7, -8
+PREC_FP64, PREC_MIXED_FP32, PREC_MIXED_FP16 = 0, 1, 2
+DAG, DEVICE_PTRS = 1, 2
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_MIXED_FP32, "fp16": PREC_MIXED_FP16}
+STATUS_NAMES = {0: "LQCD_OK", -1: "LQCD_EINVAL", -2: "LQCD_ENOMEM", -3: "LQCD_ECUDA", -4: "LQCD_ENOCONV",
+                -5: "LQCD_EBUSY", -6: "LQCD_ETIMEOUT", -7: "LQCD_ENOTFOUND", -8: "LQCD_ENOTIMPL"}
+DEFAULT_THETA = (1.0, 1.0, 1.0, -1.0)
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class DiracParams(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("csw", ctypes.c_double), ("theta_re", ctypes.c_double * 4),
+                ("theta_im", ctypes.c_double * 4), ("mu", ctypes.c_double)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("nrhs", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong), ("bytes", ctypes.c_double),
+                ("timed_launches", ctypes.c_longlong), ("timed_ms", ctypes.c_double), ("timed_bytes", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters_inner", ctypes.c_int), ("iters_outer", ctypes.c_int), ("true_resid", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"iters_inner": self.iters_inner, "iters_outer": self.iters_outer,
+                "true_resid": self.true_resid, "status": self.status}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads liblqcd.so (raises LqcdError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise LqcdError(ECUDA, f"{_build.LIB} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.lqcd_last_error.restype = ctypes.c_char_p
+    sig = {
+        "lqcd_abi_version": [],
+        "lqcd_lattice_create": [ip, ctypes.c_int, ctypes.POINTER(vp)],
+        "lqcd_lattice_destroy": [vp],
+        "lqcd_gauge_upload": [vp, vp, ip],
+        "lqcd_gauge_free": [vp, ctypes.c_int],
+        "lqcd_dirac_apply": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), vp, vp, ctypes.c_int, vp],
+        "lqcd_cg_solve": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), vp, vp,
+                          ctypes.c_int, ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
+        "lqcd_pion_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip, vp, vp,
+                           ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
+        "lqcd_pion_contract": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp],
+        "lqcd_serve_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)],
+        "lqcd_serve_gauge": [vp, ip, vp, ip],
+        "lqcd_serve_submit": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip,
+                              ctypes.POINTER(ctypes.c_uint64)],
+        "lqcd_serve_poll": [vp, ctypes.c_uint64, dp, ctypes.POINTER(SolveInfo), dp, ctypes.c_int],
+        "lqcd_serve_destroy": [vp],
+        "lqcd_profile_reset": [ctypes.c_int],
+        "lqcd_profile_read": [ctypes.POINTER(KernelStat), ctypes.c_int, ip],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().lqcd_last_error().decode()
+
+
+def _check(rc, allow=(OK,)):
+    if rc not in allow:
+        raise LqcdError(rc, last_error())
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _is_cuda_tensor(a) -> bool:
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+def _host(a, dtype=np.complex128):
+    if _is_cuda_tensor(a):
+        raise TypeError("mixing device and host buffers in one call is not supported")
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _dev_ptr(t, nreal):
+    """Device pointer of a contiguous CUDA tensor holding `nreal` doubles."""
+    if not t.is_contiguous():
+        raise ValueError("device tensors must be contiguous")
+    if t.is_complex():
+        n = t.numel() * 2
+        ok = str(t.dtype) == "torch.complex128"
+    else:
+        n = t.numel()
+        ok = str(t.dtype) == "torch.float64"
+    if not ok:
+        raise TypeError("device tensors must be complex128 or float64")
+    if n != nreal:
+        raise ValueError(f"device tensor has {n} reals, expected {nreal}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_of(t, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    import torch  # only reached for device tensors
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def dirac_params(kappa, csw, theta=DEFAULT_THETA, mu=0.0) -> DiracParams:
+    th = np.asarray(theta, dtype=np.complex128)
+    p = DiracParams()
+    p.kappa, p.csw, p.mu = float(kappa), float(csw), float(mu)
+    for k in range(4):
+        p.theta_re[k] = th[k].real
+        p.theta_im[k] = th[k].imag
+    return p
+
+
+def solver_params(tol=1e-10, maxiter=10000, precision="fp64", inner_tol=0.0, nrhs=1) -> SolverParams:
+    s = SolverParams()
+    s.tol, s.maxiter, s.inner_tol, s.nrhs = float(tol), int(maxiter), float(inner_tol), int(nrhs)
+    s.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return s
+
+
+# ---------------------------------------------------------------------------
+# the ABI
+# ---------------------------------------------------------------------------
+
+def abi_version() -> int:
+    return load().lqcd_abi_version()
+
+
+def lattice_create(dims, device=0):
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    h = ctypes.c_void_p()
+    _check(load().lqcd_lattice_create(d, int(device), ctypes.byref(h)))
+    return h
+
+
+def lattice_destroy(lat):
+    _check(load().lqcd_lattice_destroy(lat))
+
+
+def gauge_upload(lat, U) -> int:
+    u = _host(U)
+    gid = ctypes.c_int(-1)
+    _check(load().lqcd_gauge_upload(lat, u.ctypes.data_as(ctypes.c_void_p), ctypes.byref(gid)))
+    return gid.value
+
+
+def gauge_free(lat, gauge_id):
+    _check(load().lqcd_gauge_free(lat, int(gauge_id)))
+
+
+def dirac_apply(lat, gauge_id, params: DiracParams, psi, out=None, dagger=False, stream=None):
+    """out = D psi (or D^dag psi); numpy in -> numpy out, CUDA tensor in -> tensor out."""
+    flags = DAG if dagger else 0
+    if _is_cuda_tensor(psi):
+        if out is None:
+            out = psi.new_empty(psi.shape)
+        n = psi.numel() * (2 if psi.is_complex() else 1)
+        rc = load().lqcd_dirac_apply(lat, int(gauge_id), ctypes.byref(params), _dev_ptr(psi, n), _dev_ptr(out, n),
+                                     flags | DEVICE_PTRS, _stream_of(psi, stream))
+        _check(rc)
+        return out
+    p = _host(psi)
+    o = np.empty_like(p) if out is None else out
+    rc = load().lqcd_dirac_apply(lat, int(gauge_id), ctypes.byref(params), p.ctypes.data_as(ctypes.c_void_p),
+                                 o.ctypes.data_as(ctypes.c_void_p), flags, None)
+    _check(rc)
+    return o
+
+
+def cg_solve(lat, gauge_id, params: DiracParams, solver: SolverParams, b, nrhs=1, x=None, stream=None):
+    """Solves D x_j = b_j.  Returns (x, [info dicts], status)."""
+    info = (SolveInfo * nrhs)()
+    if _is_cuda_tensor(b):
+        if x is None:
+            x = b.new_empty(b.shape)
+        n = b.numel() * (2 if b.is_complex() else 1)
+        rc = load().lqcd_cg_solve(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver), _dev_ptr(b, n),
+                                  _dev_ptr(x, n), int(nrhs), info, DEVICE_PTRS, _stream_of(b, stream))
+    else:
+        bb = _host(b)
+        x = np.empty_like(bb) if x is None else x
+        rc = load().lqcd_cg_solve(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver),
+                                  bb.ctypes.data_as(ctypes.c_void_p), x.ctypes.data_as(ctypes.c_void_p), int(nrhs),
+                                  info, 0, None)
+    _check(rc, allow=(OK, ENOCONV))
+    return x, [i.as_dict() for i in info], rc
+
+
+def pion_corr(lat, gauge_id, params: DiracParams, solver: SolverParams, src, dims=None, want_prop=False,
+              device_out=None, stream=None):
+    """12-column point-source propagator + pion C(t).
+
+    Host mode (default): returns (corr ndarray, prop ndarray or None, infos, status); ``dims`` is needed
+    for the output shapes.  Device mode: ``device_out = (corr_tensor, prop_tensor_or_None)``.
+    """
+    s = (ctypes.c_int * 4)(*[int(v) for v in src])
+    info = (SolveInfo * 12)()
+    if device_out is not None:
+        corr_t, prop_t = device_out
+        rc = load().lqcd_pion_corr(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver), s,
+                                   ctypes.c_void_p(corr_t.data_ptr()),
+                                   ctypes.c_void_p(prop_t.data_ptr()) if prop_t is not None else None, info,
+                                   DEVICE_PTRS, _stream_of(corr_t, stream))
+        _check(rc, allow=(OK, ENOCONV))
+        return corr_t, prop_t, [i.as_dict() for i in info], rc
+    lx, ly, lz, lt = dims
+    corr = np.zeros(lt)
+    prop = np.zeros((12, lt, lz, ly, lx, 4, 3), dtype=np.complex128) if want_prop else None
+    rc = load().lqcd_pion_corr(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver), s,
+                               corr.ctypes.data_as(ctypes.c_void_p),
+                               prop.ctypes.data_as(ctypes.c_void_p) if prop is not None else None, info, 0, None)
+    _check(rc, allow=(OK, ENOCONV))
+    return corr, prop, [i.as_dict() for i in info], rc
+
+
+def pion_contract(lat, prop, src_t, T=None, corr=None, stream=None):
+    """C(t) from 12 host-layout propagator columns (numpy or CUDA tensor)."""
+    if _is_cuda_tensor(prop):
+        n = prop.numel() * (2 if prop.is_complex() else 1)
+        if corr is None:
+            raise ValueError("device mode needs a float64 CUDA tensor `corr` of length T")
+        _check(load().lqcd_pion_contract(lat, _dev_ptr(prop, n), int(src_t), ctypes.c_void_p(corr.data_ptr()),
+                                         DEVICE_PTRS, _stream_of(prop, stream)))
+        return corr
+    p = _host(prop)
+    T = p.shape[1] if T is None else T
+    c = np.zeros(T)
+    _check(load().lqcd_pion_contract(lat, p.ctypes.data_as(ctypes.c_void_p), int(src_t),
+                                     c.ctypes.data_as(ctypes.c_void_p), 0, None))
+    return c
+
+
+# ---------------------------------------------------------------------------
+# launch accounting
+# ---------------------------------------------------------------------------
+
+def profile_reset(timing=False):
+    _check(load().lqcd_profile_reset(1 if timing else 0))
+
+
+def profile_read() -> dict:
+    """{kernel name: {launches, bytes, timed_launches, timed_ms, timed_bytes}}."""
+    n = ctypes.c_int(0)
+    _check(load().lqcd_profile_read(None, 0, ctypes.byref(n)))
+    buf = (KernelStat * max(1, n.value))()
+    _check(load().lqcd_profile_read(buf, n.value, ctypes.byref(n)))
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "bytes": buf[i].bytes,
+                                   "timed_launches": buf[i].timed_launches, "timed_ms": buf[i].timed_ms,
+                                   "timed_bytes": buf[i].timed_bytes} for i in range(n.value)}
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+def serve_create(device=0, hbm_budget_bytes=0, max_slots=4):
+    h = ctypes.c_void_p()
+    _check(load().lqcd_serve_create(int(device), int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+    return h
+
+
+def serve_gauge(srv, dims, U) -> int:
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    u = _host(U)
+    gid = ctypes.c_int(-1)
+    _check(load().lqcd_serve_gauge(srv, d, u.ctypes.data_as(ctypes.c_void_p), ctypes.byref(gid)))
+    return gid.value
+
+
+def serve_submit(srv, gauge_id, params: DiracParams, solver: SolverParams, src) -> int:
+    s = (ctypes.c_int * 4)(*[int(v) for v in src])
+    t = ctypes.c_uint64(0)
+    _check(load().lqcd_serve_submit(srv, int(gauge_id), ctypes.byref(params), ctypes.byref(solver), s,
+                                    ctypes.byref(t)))
+    return t.value
+
+
+def serve_poll(srv, ticket, T, timeout_ms=0):
+    """Returns (status, corr, infos, timestamps); status may be EBUSY / ETIMEOUT (then the rest is None)."""
+    corr = np.zeros(T)
+    info = (SolveInfo * 12)()
+    ts = (ctypes.c_double * 4)()
+    rc = load().lqcd_serve_poll(srv, ctypes.c_uint64(ticket), corr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                info, ts, int(timeout_ms))
+    if rc in (EBUSY, ETIMEOUT):
+        return rc, None, None, None
+    _check(rc, allow=(OK, ENOCONV))
+    return rc, corr, [i.as_dict() for i in info], list(ts)
+
+
+def serve_destroy(srv):
+    _check(load().lqcd_serve_destroy(srv))
