@@ -1,0 +1,476 @@
+#!/usr/bin/env python
+"""Benchmark of the Wilson-clover point-source propagator path on GB300.
+
+One step = one 12-column point-source propagator and pion correlator
+(lqcd_pion_corr) on a 32^3 x 64 lattice with seeded synthetic links
+U = exp(i 0.4 H), kappa = 0.132, csw = 1.7: the 12 spin-colour right-hand
+sides batched per launch, FP16 (+ per-site scale) spinors and FP16
+reconstruct-12 links and clover in the inner CG, FP32 arithmetic, FP64
+reliable updates and an FP64 final true residual <= 1e-10 per column.
+
+value  = right-hand sides solved to 1e-10 per second over the whole job
+         (12 per step per GPU), inputs resident in HBM, CUDA-event timed.
+e2e    = the same through the host-pointer API: every step uploads the
+         gauge field from pinned host memory (lqcd_gauge_upload, which also
+         rebuilds the clover field), solves, and copies the 12 propagator
+         columns and C(t) back to pinned host memory.
+roofline: the FP16 hopping kernels (dominant) timed live with CUDA events
+         on their launch stream inside the timed region; algorithmic bytes
+         counted by the library per launch.
+
+Multi-GPU: replicas only (independent propagators per GPU, no collective on
+the data path); run under torch.distributed.run for N > 1.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the
+same workload (see cpu_baseline_measure).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash HBM GB/s (%peak); mixed-vs-FP64 solves/s at 1e-10; served p50/p99"
+WORKLOAD = {
+    "workload": "pion propagator 32^3x64, 12 RHS batched, FP16 storage / FP32 math / FP64 outer, tol 1e-10",
+    "lattice": [32, 32, 32, 64],
+    "eps": 0.4,
+    "kappa": 0.132,
+    "csw": 1.7,
+    "seed": 1,
+    "src": [0, 0, 0, 0],
+    "nrhs": 12,
+    "tol": 1e-10,
+    "precision": "fp16",
+    "l2": "inputs larger than L2 (~10 GB working set vs 129 MB L2); no flush needed",
+}
+NOMINAL_HBM_GBS = 8000.0
+# Oracle cost model for the CPU baseline: one CGNR iteration costs two
+# full-lattice applications of D (D and D^dag).  The number of iterations is
+# taken as the normal-operator applications the GPU FP64 solver needs on this
+# workload (measured on GB300); the oracle's unpreconditioned
+# CGNR needs more, so the baseline over-states the oracle's speed.
+ORACLE_ITERS = 360
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def hbm_peak():
+    p = peaks()
+    if "hbm_gbs" in p:
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if _cuda_ok() else "gloo")
+    return world, rank, local
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda_ok() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands
+# ---------------------------------------------------------------------------
+def cpu_baseline_measure(U, sample_frac=0.25):
+    """Times the oracle's D at a fixed quarter of the sites of the workload.
+
+    The oracle's full D computes the clover field at every site and then
+    applies the operator; oracle.dirac_sites does both per listed site, so a
+    quarter of the sites is a quarter of the work.  Returns (solves/s, seconds
+    of the sample, description)."""
+    import oracle
+    from paper_2503_16994_gb300 import inputs
+    dims = tuple(WORKLOAD["lattice"])
+    V = inputs.volume(dims)
+    psi = inputs.spinor_field(dims, seed=2)
+    nsample = int(V * sample_frac)
+    sites = np.arange(0, V, int(round(1 / sample_frac)))[:nsample]
+    t0 = time.perf_counter()
+    oracle.dirac_sites(dims, U, WORKLOAD["kappa"], WORKLOAD["csw"], psi, sites)
+    dt = time.perf_counter() - t0
+    t_D = dt * V / len(sites)
+    solve_s = 2.0 * ORACLE_ITERS * t_D
+    desc = (f"oracle D (FP64, 1 thread) at {len(sites)} of {V} sites of the 32^3x64 workload in {dt:.2f} s "
+            f"-> {t_D:.1f} s per full-lattice D; one solve costed as 2 x {ORACLE_ITERS} D applications")
+    return 1.0 / solve_s, dt, desc
+
+
+# ---------------------------------------------------------------------------
+# Dslash alone: the even-odd operator Dhat in each storage format
+# ---------------------------------------------------------------------------
+DSLASH_LEGS = [("fp16", 12, 20), ("fp16", 1, 100), ("fp32", 12, 10), ("fp64", 1, 10)]
+
+
+def dslash_measure(lqcd, lat, gid, dp, dims, legs=DSLASH_LEGS):
+    """Times Dhat (two hopping kernels per application) with lqcd_schur_apply.
+
+    Per leg: `repeat` applications to the same even-parity field, each hopping
+    launch timed with CUDA events on its stream; GB/s = algorithmic bytes /
+    time of the hopping kernels (spinor in, out and self once per RHS, 8
+    links and one clover block pair per site)."""
+    import torch
+    from paper_2503_16994_gb300 import inputs
+    V = inputs.volume(dims)
+    peak, kind = hbm_peak()
+    out = {}
+    for prec, nrhs, repeat in legs:
+        x = torch.randn(nrhs * V * 24, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        lqcd.schur_apply(lat, gid, dp, x, precision=prec, nrhs=nrhs, repeat=2, out=y)  # warm-up
+        torch.cuda.synchronize()
+        lqcd.profile_reset(timing=True)
+        lqcd.schur_apply(lat, gid, dp, x, precision=prec, nrhs=nrhs, repeat=repeat, out=y)
+        prof = lqcd.profile_read()
+        hop = {k: v for k, v in prof.items() if k.startswith("hop_")}
+        ms = sum(v["timed_ms"] for v in hop.values())
+        by = sum(v["timed_bytes"] for v in hop.values())
+        n = sum(v["timed_launches"] for v in hop.values())
+        gbs = by / (ms / 1e3) / 1e9
+        sites = V // 2
+        out[f"{prec}_{nrhs}rhs"] = {
+            "GB/s": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
+            "frac_of_nominal_8TBs": round(gbs / NOMINAL_HBM_GBS, 4),
+            "us_per_hop": round(ms * 1e3 / n, 2), "hops": n,
+            "per_kernel_us": {k: round(v["timed_ms"] * 1e3 / max(1, v["timed_launches"]), 2) for k, v in hop.items()},
+            # hop: 1320 flop per output site and RHS, plus 504 for the fused clover pair
+            "GFLOP/s": round((1320 + 504) * sites * nrhs * n / (ms / 1e3) / 1e9, 1)}
+        del x, y
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_dslash_only(args):
+    """Standalone Dslash timing on a chosen lattice (used for ncu captures)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2503_16994_gb300 import inputs
+    from paper_2503_16994_gb300 import lqcd
+    __graft_entry__.build()
+    dims = tuple(int(v) for v in args.lattice.split(","))
+    U = inputs.gauge_field(dims, WORKLOAD["eps"], seed=WORKLOAD["seed"], workers=None)
+    lat = lqcd.lattice_create(dims)
+    gid = lqcd.gauge_upload(lat, U)
+    dp = lqcd.dirac_params(WORKLOAD["kappa"], WORKLOAD["csw"])
+    legs = [(args.precision, args.nrhs, args.repeat)]
+    res = dslash_measure(lqcd, lat, gid, dp, dims, legs)
+    lqcd.lattice_destroy(lat)
+    print(json.dumps({"dslash": res, "lattice": list(dims)}))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import __graft_entry__
+    from paper_2503_16994_gb300 import inputs
+    from paper_2503_16994_gb300 import lqcd
+
+    world, rank, local = dist_setup()
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    lqcd.load()
+    torch.cuda.set_device(local)
+    dims = tuple(WORKLOAD["lattice"])
+    T = dims[3]
+    V = inputs.volume(dims)
+    nrhs = WORKLOAD["nrhs"]
+    U = inputs.gauge_field(dims, WORKLOAD["eps"], seed=WORKLOAD["seed"] + rank, workers=None)
+    lat = lqcd.lattice_create(dims, device=local)
+    gid = lqcd.gauge_upload(lat, U)
+    dp = lqcd.dirac_params(WORKLOAD["kappa"], WORKLOAD["csw"])
+    sp = lqcd.solver_params(tol=WORKLOAD["tol"], maxiter=20000, precision=WORKLOAD["precision"])
+    src = tuple(WORKLOAD["src"])
+    corr = torch.zeros(T, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    infos_last = None
+
+    def step():
+        nonlocal infos_last
+        _, _, infos, rc = lqcd.pion_corr(lat, gid, dp, sp, src, device_out=(corr, None), stream=stream)
+        if rc != lqcd.OK:
+            raise RuntimeError(f"solve did not converge: {infos}")
+        infos_last = infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    lqcd.profile_reset(timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()  # brackets the timed region for ncu --profile-from-start off
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    prof = lqcd.profile_read()
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world)
+    value = nrhs * args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel family: the FP16 hopping kernels
+    hop = {k: v for k, v in prof.items() if k.startswith("hop_f16")}
+    hop_ms = sum(v["timed_ms"] for v in hop.values())
+    hop_bytes = sum(v["timed_bytes"] for v in hop.values())
+    hop_launches = sum(v["timed_launches"] for v in hop.values())
+    total_ms = sum(v["timed_ms"] for v in prof.values())
+    achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
+    peak, peak_kind = hbm_peak()
+    launches = int(sum(v["launches"] for v in prof.values()))
+    per_kernel = {k: {"launches": v["launches"], "ms": round(v["timed_ms"], 3),
+                      "GB/s": round(v["timed_bytes"] / max(v["timed_ms"], 1e-9) / 1e6, 1)}
+                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["timed_ms"])}
+
+    # e2e through the host-pointer API (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        Upin = torch.from_numpy(U.reshape(-1).view(np.float64)).pin_memory()
+        prop_pin = torch.empty(12 * V * 24, dtype=torch.float64).pin_memory()
+        corr_pin = torch.empty(T, dtype=torch.float64).pin_memory()
+        import ctypes
+        lib = lqcd.load()
+        info = (lqcd.SolveInfo * 12)()
+        s4 = (ctypes.c_int * 4)(*src)
+
+        def e2e_step():
+            g = ctypes.c_int(-1)
+            lqcd._check(lib.lqcd_gauge_upload(lat, ctypes.c_void_p(Upin.data_ptr()), ctypes.byref(g)))
+            rc = lib.lqcd_pion_corr(lat, g.value, ctypes.byref(dp), ctypes.byref(sp), s4,
+                                    ctypes.c_void_p(corr_pin.data_ptr()), ctypes.c_void_p(prop_pin.data_ptr()),
+                                    info, 0, None)
+            lqcd._check(rc)
+            lqcd._check(lib.lqcd_gauge_free(lat, g.value))
+
+        e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = max(1, args.steps // 2)
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": nrhs * ke * world / te, "unit": "solves/s", "h2d_bytes_per_step": 72 * V * 8 + 16,
+               "d2h_bytes_per_step": 12 * V * 24 * 8 + T * 8, "steps": ke,
+               "api": "lqcd_gauge_upload + lqcd_pion_corr (host prop and corr) + lqcd_gauge_free"}
+
+    # plain FP64 GPU CG on the same lattice and sources
+    fp64 = None
+    if not args.no_fp64:
+        sp64 = lqcd.solver_params(tol=WORKLOAD["tol"], maxiter=20000, precision="fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, infos64, rc = lqcd.pion_corr(lat, gid, dp, sp64, src, device_out=(corr, None), stream=stream)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        fp64 = {"solves_per_s": nrhs / t64, "ms_per_step": t64 * 1e3, "converged": rc == lqcd.OK,
+                "iters_max": max(i["iters_inner"] for i in infos64),
+                "true_resid_max": max(i["true_resid"] for i in infos64)}
+
+    dslash = None if args.no_dslash else dslash_measure(lqcd, lat, gid, dp, dims)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, desc = cpu_baseline_measure(U)
+        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**WORKLOAD, "parallelism": f"replicas x{world} (independent propagators)",
+                       "storage": "spinors FP16 + per-site FP32 scale, links FP16 recon-12, clover FP16; "
+                                  "FP32 arithmetic; FP64 reliable updates and final residual"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "hop_f16_* (hopclov + selfclov)",
+                         "peak_source": f"{peak_kind} hbm_gbs", "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS,
+                         "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None},
+            "dslash": dslash, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "fp64_gpu": fp64, "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
+            "iters": {"inner_max": max(i["iters_inner"] for i in infos_last),
+                      "outer_max": max(i["iters_outer"] for i in infos_last),
+                      "true_resid_max": max(i["true_resid"] for i in infos_last)},
+            "kernels": per_kernel,
+        }
+        print(json.dumps(out))
+    lqcd.lattice_destroy(lat)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2503_16994_gb300 import inputs
+    oracle.build()
+    dims = tuple(WORKLOAD["lattice"])
+    U = inputs.gauge_field(dims, WORKLOAD["eps"], seed=WORKLOAD["seed"], workers=None)
+    # a step is the oracle's D on a sixteenth of the sites (about 2 s)
+    for _ in range(args.warmup):
+        cpu_baseline_measure(U, sample_frac=1 / 16)
+    vals, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, dt, desc = cpu_baseline_measure(U, sample_frac=1 / 16)
+        vals.append(v)
+        secs += dt
+    value = float(np.median(vals))
+    out = {"metric": METRIC, "impl": "reference", "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {**WORKLOAD, "parallelism": "1 host thread"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "kind": "oracle", "cores": 1, "sample": desc},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dslash", action="store_true")
+    ap.add_argument("--dslash-only", action="store_true", help="time only the Dslash on --lattice")
+    ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--precision", default="fp16")
+    ap.add_argument("--nrhs", type=int, default=12)
+    ap.add_argument("--repeat", type=int, default=20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.dslash_only:
+        run_dslash_only(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -158,6 +158,23 @@ int lqcd_gauge_free(lqcd_lattice lat, int gauge_id);
 int lqcd_dirac_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
                      const double *psi_in, double *psi_out, int flags, void *stream);
 
+/* The even-odd preconditioned operator used by the solver (the Schur
+ * complement of D on the even sites; the paper's Dw! restricted to one
+ * parity block, Sec. 3.3):
+ *   Dhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe     (Dhat^dag = g5 Dhat g5 with LQCD_DAG)
+ * where A is the clover site term and H the hopping term of D, applied in
+ * the storage format of `precision` (LQCD_PREC_*: FP64; FP32; FP16 spinors
+ * with a per-site scale, FP16 reconstruct-12 links and FP16 clover, FP32
+ * arithmetic).  in, out: nrhs full-lattice fields in the host layout (host
+ * memory, or device memory with LQCD_DEVICE_PTRS); only the even sites of in
+ * are read (converted to `precision` first); out receives Dhat in on the even
+ * sites (converted back to FP64) and zero on the odd sites.  repeat >= 1:
+ * the operator is applied `repeat` times to the same input (same result),
+ * so its kernels can be timed with lqcd_profile_*.
+ * Errors: LQCD_EINVAL, LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_schur_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, int precision,
+                     const double *in, double *out, int nrhs, int repeat, int flags, void *stream);
+
 /* Solves D x_j = b_j for j = 0..nrhs-1 (CG! of Sec. 3.3) by CG on the normal
  * equations of the even-odd preconditioned (Schur) operator
  *   Dhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe

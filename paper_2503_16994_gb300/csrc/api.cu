@@ -179,6 +179,36 @@ int lqcd_dirac_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp
     API_CATCH
 }
 
+int lqcd_schur_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, int precision, const double *in,
+                     double *out, int nrhs, int repeat, int flags, void *stream)
+{
+    if (!lat || !in || !out) return fail(LQCD_EINVAL, "null argument");
+    if (nrhs < 1 || repeat < 1) return fail(LQCD_EINVAL, "nrhs and repeat must be >= 1");
+    if (precision < LQCD_PREC_FP64 || precision > LQCD_PREC_MIXED_FP16) return fail(LQCD_EINVAL, "unknown precision");
+    if (int rc = check_params(dp)) return rc;
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    const size_t bytes = sizeof(double) * 24 * (size_t)lat->V * nrhs;
+    const double *id = in;
+    double *od = out;
+    if (!(flags & LQCD_DEVICE_PTRS)) {
+        lat->staging.ensure(bytes);
+        lat->staging2.ensure(bytes);
+        LQCD_CUDA(cudaMemcpyAsync(lat->staging.p, in, bytes, cudaMemcpyHostToDevice, st));
+        id = lat->staging.as<const double>();
+        od = lat->staging2.as<double>();
+    }
+    schur_apply_dev(lat, *it->second, *dp, precision, id, od, nrhs, repeat, (flags & LQCD_DAG) != 0, st);
+    if (!(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(out, od, bytes, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    return LQCD_OK;
+    API_CATCH
+}
+
 int lqcd_cg_solve(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, const lqcd_solver_params *sp,
                   const double *b, double *x, int nrhs, lqcd_solve_info *info, int flags, void *stream)
 {

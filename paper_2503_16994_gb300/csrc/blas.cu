@@ -66,6 +66,19 @@ void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, Spino
     LQCD_CHECK_LAUNCH();
 }
 
+template <class SI, class SO>
+void launch_convert(long vh, int nrhs, SpinorField<SI> in, SpinorField<SO> out, cudaStream_t st)
+{
+    ProfScope prof("convert", double(vh) * nrhs * (spinor_bytes<SI>() + spinor_bytes<SO>()), st);
+    convert_kernel<SI, SO><<<unsigned(ntiles_of(vh) * nrhs), kBlock, 0, st>>>(int(vh), nrhs, in, out);
+    LQCD_CHECK_LAUNCH();
+}
+
+template void launch_convert<F64, F64>(long, int, SpinorField<F64>, SpinorField<F64>, cudaStream_t);
+template void launch_convert<F64, F32>(long, int, SpinorField<F64>, SpinorField<F32>, cudaStream_t);
+template void launch_convert<F64, F16>(long, int, SpinorField<F64>, SpinorField<F16>, cudaStream_t);
+template void launch_convert<F32, F64>(long, int, SpinorField<F32>, SpinorField<F64>, cudaStream_t);
+template void launch_convert<F16, F64>(long, int, SpinorField<F16>, SpinorField<F64>, cudaStream_t);
 template void launch_er_update<F64, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F64>,
                                          SpinorField<F64>, cudaStream_t);
 template void launch_er_update<F32, F32>(const VecArgs &, SpinorField<F32>, SpinorField<F32>, SpinorField<F32>,

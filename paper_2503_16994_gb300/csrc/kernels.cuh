@@ -313,6 +313,16 @@ __global__ void __launch_bounds__(128) cg_r_replace(VecArgs v, SpinorField<F64> 
     reduce_finish(v.red, j, tile, v.ntiles, n2);
 }
 
+// out = in, converted between storage formats
+template <class SI, class SO>
+__global__ void __launch_bounds__(128) convert_kernel(int vh, int nrhs, SpinorField<SI> in, SpinorField<SO> out)
+{
+    const int j = blockIdx.x % nrhs, tile = blockIdx.x / nrhs;
+    const int i = tile * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    store_spinor<SO, double>(out, j, i, load_spinor<SI, double>(in, j, i));
+}
+
 // out = C in (clover blocks of parity `parity`)
 template <class S, class C>
 __global__ void __launch_bounds__(128) clover_apply_kernel(int vh, int nrhs, int parity, CloverField<C> cl,

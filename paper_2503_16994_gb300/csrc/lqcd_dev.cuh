@@ -309,6 +309,10 @@ __device__ __forceinline__ double store_spinor(const SpinorField<S> &f, int j, i
             fv[q] = float(v[q]);
             mx = fmaxf(mx, fabsf(fv[q]));
         }
+        // Sites whose largest component is below 1e-30 are stored as zero:
+        // the exponentially decaying point-source propagator leaves FP32
+        // denormals far from the source, where 1/mx would overflow.
+        if (!(mx >= 1e-30f)) mx = 0.f;
         float inv = mx > 0.f ? 1.0f / mx : 0.f;
         f.scale[(long)j * f.stride + i] = mx;
         float acc = 0.f;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -137,6 +138,8 @@ template <class S> constexpr const char *prec_name() { return S::W == 2 ? "f64" 
 
 inline int ntiles_of(long vh) { return int((vh + kBlock - 1) / kBlock); }
 
+
+
 // gauge / clover setup (field_ops.cu)
 void gauge_repack(lqcd_lattice_s *lat, GaugeSet &g, const double *U_dev_aos, cudaStream_t st);
 CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st);
@@ -175,7 +178,12 @@ template <class S, class C>
 void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
                          cudaStream_t st);
 
+template <class SI, class SO>
+void launch_convert(long vh, int nrhs, SpinorField<SI> in, SpinorField<SO> out, cudaStream_t st);
+
 // solver (solver.cu)
+void schur_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, int precision, const double *in,
+                     double *out, int nrhs, int repeat, bool dag, cudaStream_t st);
 void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
                      bool dag, cudaStream_t st);
 int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,

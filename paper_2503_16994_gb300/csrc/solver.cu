@@ -279,6 +279,25 @@ struct Solver {
         launch_hop(a, RESID, false, true, st);
     }
 
+    // w = Dhat p (or Dhat^dag p), no reductions, every RHS
+    void apply_schur(bool dag)
+    {
+        HopArgs<W, W, W> a = hw;
+        a.parity = 1;
+        a.in = p;
+        a.out = t;
+        a.clov = aiw;
+        a.coef = kappa;
+        launch_hop(a, HOP_CLOV, dag, false, st);
+        a.parity = 0;
+        a.in = t;
+        a.self = p;
+        a.out = w;
+        a.clov = aw;
+        a.coef = -kappa;
+        launch_hop(a, SELF_CLOV, dag, false, st);
+    }
+
     void pull_states()
     {
         LQCD_CUDA(cudaMemcpyAsync(ws.host_state, S, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -288,6 +307,13 @@ struct Solver {
     void push_states()
     {
         LQCD_CUDA(cudaMemcpyAsync(S, ws.host_state, sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, st));
+    }
+
+    bool any_status(int st_) const
+    {
+        for (int j = 0; j < nrhs; ++j)
+            if (ws.host_state[j].status == st_) return true;
+        return false;
     }
 
     bool all_finished() const
@@ -307,17 +333,35 @@ struct Solver {
         prepare(0.5 * tol, delta, sp.maxiter);
         reliable_update();
         half2();
-        const int chunk = 8;
+        // Large batches: read the states after every half-iteration and launch
+        // the FP64 update only when some RHS asked for it (a gated-off launch
+        // of the FP64 kernels still schedules every block; the host round trip
+        // costs ~15 us against milliseconds of work).  Small batches: gated
+        // launches are cheap, so poll every few iterations only.
+        const bool poll_each = long(lat->vh) * nrhs >= (1L << 20);
+        const int chunk = poll_each ? 1 : 8;
         for (int attempt = 0; attempt < 4; ++attempt) {
             long guard = (long)sp.maxiter + 64;
-            for (long it = 0; it < guard; it += chunk) {
+            bool finished = false;
+            for (long it = 0; it < guard && !finished; it += chunk) {
                 for (int k = 0; k < chunk; ++k) {
                     half1();
-                    reliable_update();
+                    if (poll_each) {
+                        pull_states();
+                        if (all_finished()) {
+                            finished = true;
+                            break;
+                        }
+                        if (any_status(ST_UPDATE)) reliable_update();
+                    } else {
+                        reliable_update();
+                    }
                     half2();
                 }
-                pull_states();
-                if (all_finished()) break;
+                if (!poll_each) {
+                    pull_states();
+                    finished = all_finished();
+                }
             }
             finish();
             pull_states();
@@ -403,6 +447,36 @@ void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
     a.out = oo;
     launch_hop(a, SELF_CLOV, dag, false, st);
     spinor_from_soa(lat, out, 1, oe, oo, st);
+}
+
+template <class W, class E>
+static void schur_apply_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, const lqcd_dirac_params &dp, int prec,
+                             const double *in, double *out, int nrhs, int repeat, bool dag, cudaStream_t st)
+{
+    Workspace &ws = workspace<W, E>(lat, nrhs, prec, st);
+    Solver<W, E> s(lat, ws, g, cl, dp, nrhs, st);
+    spinor_to_soa(lat, in, nrhs, s.b_e, s.b_o, st);
+    launch_convert<F64, W>(lat->vh, nrhs, s.b_e, s.p, st);
+    for (int k = 0; k < repeat; ++k) s.apply_schur(dag);
+    launch_convert<W, F64>(lat->vh, nrhs, s.w, s.x_e, st);
+    LQCD_CUDA(cudaMemsetAsync(ws.x_o.p, 0, ws.x_o.bytes, st));
+    spinor_from_soa(lat, out, nrhs, s.x_e, s.x_o, st);
+}
+
+void schur_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, int precision, const double *in,
+                     double *out, int nrhs, int repeat, bool dag, cudaStream_t st)
+{
+    CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
+    switch (precision) {
+    case LQCD_PREC_FP64: schur_apply_prec<F64, F64>(lat, g, cl, dp, precision, in, out, nrhs, repeat, dag, st); break;
+    case LQCD_PREC_MIXED_FP32:
+        schur_apply_prec<F32, F32>(lat, g, cl, dp, precision, in, out, nrhs, repeat, dag, st);
+        break;
+    case LQCD_PREC_MIXED_FP16:
+        schur_apply_prec<F16, F32>(lat, g, cl, dp, precision, in, out, nrhs, repeat, dag, st);
+        break;
+    default: throw Error{LQCD_EINVAL, "unknown precision"};
+    }
 }
 
 int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,

@@ -135,14 +135,23 @@ def _gauge_chunk(args):
     return expm_i_hermitian(eps * np.einsum("sma,aij->smij", h, lam))
 
 
-def gauge_field(dims, eps: float, seed: int, chunk_sites: int = 1 << 16, workers: int | None = None) -> np.ndarray:
+def _spawn_safe() -> bool:
+    """True when spawned workers can re-import the main module (not a stdin script)."""
+    import sys
+    path = getattr(sys.modules.get("__main__"), "__file__", None)
+    return path is None or os.path.exists(path)
+
+
+def gauge_field(dims, eps: float, seed: int, chunk_sites: int = 1 << 16, workers: int | None = 1) -> np.ndarray:
     """Synthetic links U_mu(x) = exp(i eps H), shape (T, Z, Y, X, 4, 3, 3).
 
     ``dims = (Lx, Ly, Lz, T)``.  Sites are processed in chunks of
     ``chunk_sites`` (keep the default for reproducible values: the scaling
     step of the exponential is chosen per chunk); large fields are spread over
-    a process pool (spawn context) of ``workers`` processes (default: up to 16
-    cores).
+    a process pool (spawn context) of ``workers`` processes when ``workers``
+    > 1, or ``None`` for up to 16 cores.  A pool re-imports the caller's main
+    module in every worker, so pass ``workers`` only from a script whose main
+    code sits under ``if __name__ == "__main__":`` (or from pytest).
     """
     lx, ly, lz, lt = dims
     nsite = volume(dims)
@@ -150,6 +159,8 @@ def gauge_field(dims, eps: float, seed: int, chunk_sites: int = 1 << 16, workers
     jobs = [(s0, min(nsite, s0 + chunk_sites), eps, seed) for s0 in range(0, nsite, chunk_sites)]
     if workers is None:
         workers = min(16, len(os.sched_getaffinity(0))) if len(jobs) >= 8 else 1
+    if workers > 1 and not _spawn_safe():
+        workers = 1
     if workers > 1 and len(jobs) > 1:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(workers) as pool:

@@ -83,6 +83,8 @@ def load():
         "lqcd_gauge_upload": [vp, vp, ip],
         "lqcd_gauge_free": [vp, ctypes.c_int],
         "lqcd_dirac_apply": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), vp, vp, ctypes.c_int, vp],
+        "lqcd_schur_apply": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.c_int, vp, vp, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_int, vp],
         "lqcd_cg_solve": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), vp, vp,
                           ctypes.c_int, ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
         "lqcd_pion_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip, vp, vp,
@@ -216,6 +218,25 @@ def dirac_apply(lat, gauge_id, params: DiracParams, psi, out=None, dagger=False,
     rc = load().lqcd_dirac_apply(lat, int(gauge_id), ctypes.byref(params), p.ctypes.data_as(ctypes.c_void_p),
                                  o.ctypes.data_as(ctypes.c_void_p), flags, None)
     _check(rc)
+    return o
+
+
+def schur_apply(lat, gauge_id, params: DiracParams, psi, precision="fp64", nrhs=1, repeat=1, dagger=False,
+                out=None, stream=None):
+    """Even-odd preconditioned operator Dhat (or Dhat^dag) on the even sites of psi, in `precision`."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    flags = DAG if dagger else 0
+    if _is_cuda_tensor(psi):
+        out = psi.new_empty(psi.shape) if out is None else out
+        n = psi.numel() * (2 if psi.is_complex() else 1)
+        _check(load().lqcd_schur_apply(lat, int(gauge_id), ctypes.byref(params), prec, _dev_ptr(psi, n),
+                                       _dev_ptr(out, n), int(nrhs), int(repeat), flags | DEVICE_PTRS,
+                                       _stream_of(psi, stream)))
+        return out
+    p = _host(psi)
+    o = np.empty_like(p) if out is None else out
+    _check(load().lqcd_schur_apply(lat, int(gauge_id), ctypes.byref(params), prec, p.ctypes.data_as(ctypes.c_void_p),
+                                   o.ctypes.data_as(ctypes.c_void_p), int(nrhs), int(repeat), flags, None))
     return o
 
 

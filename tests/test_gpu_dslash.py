@@ -100,7 +100,7 @@ def test_dslash_fp64_full_size_sampled(lq):
     import torch
     dims = (32, 32, 32, 64)
     kappa, csw = 0.132, 1.7
-    U = inputs.gauge_field(dims, 0.4, seed=1)
+    U = inputs.gauge_field(dims, 0.4, seed=1, workers=None)
     psi = inputs.spinor_field(dims, seed=2)
     lat = lq.lattice_create(dims)
     try:

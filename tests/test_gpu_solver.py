@@ -179,7 +179,7 @@ def test_zero_source_and_bad_arguments(lq):
         lq.lattice_destroy(lat)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
 def test_propagator_16x32_full_size(lq, prec):
     """16^3 x 32, eps = 0.4, kappa = 0.130, csw = 1.5: the 12-column propagator and C(t).
 
@@ -188,7 +188,7 @@ def test_propagator_16x32_full_size(lq, prec):
     C(t) equal to the oracle's contraction of the returned columns.
     """
     dims, kappa, csw = (16, 16, 16, 32), 0.130, 1.5
-    U = inputs.gauge_field(dims, 0.4, seed=1)
+    U = inputs.gauge_field(dims, 0.4, seed=1, workers=None)
     src = (0, 0, 0, 0)
     lat = lq.lattice_create(dims)
     try:
