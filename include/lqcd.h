@@ -235,6 +235,16 @@ int lqcd_profile_reset(int enable_timing);
  * kinds seen.  Waits for the timed launches to complete. */
 int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count);
 
+/* Autotuning decisions taken so far in this process, as a JSON array
+ * written into buf (len bytes, NUL-terminated).  Each entry names a kernel,
+ * the problem (sites per parity, right-hand sides) and the chosen shape
+ * (right-hand sides per thread, threads per block) with its time.  The
+ * hopping kernels of the FP32/FP16 formats time 1..4 right-hand sides per
+ * thread on their first launch for each problem and keep the fastest
+ * (environment variable LQCD_HOP_NR forces a value).  Returns LQCD_EINVAL
+ * if buf is too small (the text is truncated). */
+int lqcd_tune_report(char *buf, size_t len);
+
 /* ---------------- serving loop (continuous batching) ------------------- */
 
 /* A server owns one device thread that admits propagator requests

@@ -1,9 +1,153 @@
 // Launcher for the hopping kernel; included once per storage precision so
 // the instantiations compile in parallel translation units.
 #pragma once
+#include <cstdlib>
+
+#include "hopfast.cuh"
 #include "lqcd_impl.h"
 
 namespace lqcd {
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{d, unsigned(m), l};
+}
+
+template <class S, int NR, int MODE, bool DAG, bool NORM>
+static void hopf_go(const FastHop<S> &f, cudaStream_t st)
+{
+    const int ngr = (f.nrhs + NR - 1) / NR;
+    const unsigned grid = unsigned(f.ntiles * ((ngr + f.gpb - 1) / f.gpb));
+    hopf_kernel<S, NR, MODE, DAG, NORM><<<grid, kBlock, 0, st>>>(f);
+}
+
+template <class S, int NR>
+static void hopf_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st)
+{
+    if (mode == HOP_CLOV) {
+        if (dag) norm ? hopf_go<S, NR, HOP_CLOV, true, true>(f, st) : hopf_go<S, NR, HOP_CLOV, true, false>(f, st);
+        else norm ? hopf_go<S, NR, HOP_CLOV, false, true>(f, st) : hopf_go<S, NR, HOP_CLOV, false, false>(f, st);
+    } else {
+        if (dag) norm ? hopf_go<S, NR, SELF_CLOV, true, true>(f, st) : hopf_go<S, NR, SELF_CLOV, true, false>(f, st);
+        else norm ? hopf_go<S, NR, SELF_CLOV, false, true>(f, st) : hopf_go<S, NR, SELF_CLOV, false, false>(f, st);
+    }
+}
+
+template <class S>
+static void hopf_launch(const FastHop<S> &f, int nr, int mode, bool dag, bool norm, cudaStream_t st)
+{
+    if constexpr (std::is_same<S, F64>::value) {
+        hopf_dispatch<S, 1>(f, mode, dag, norm, st);
+    } else {
+        switch (nr) {
+        case 1: hopf_dispatch<S, 1>(f, mode, dag, norm, st); break;
+        case 2: hopf_dispatch<S, 2>(f, mode, dag, norm, st); break;
+        default: hopf_dispatch<S, 3>(f, mode, dag, norm, st); break;
+        }
+    }
+}
+
+// Autotuned shape: right-hand sides per thread (NR) and groups of NR per
+// block (GPB), keyed by (sites, nrhs, format, mode).  The first launch of a
+// key times the candidates (no reductions, same stream and buffers: every
+// candidate writes the output the real launch then overwrites) and keeps
+// the fastest.  LQCD_HOP_NR / LQCD_HOP_GPB force a value.
+struct HopShape {
+    int nr, gpb;
+};
+
+template <class S>
+static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, HopShape> table;
+    const char *env_nr = std::getenv("LQCD_HOP_NR");
+    const char *env_gpb = std::getenv("LQCD_HOP_GPB");
+    if (env_nr || env_gpb) {
+        int nr = env_nr ? std::atoi(env_nr) : 1, gpb = env_gpb ? std::atoi(env_gpb) : 1;
+        return HopShape{std::min(std::max(nr, 1), 4), std::max(gpb, 1)};
+    }
+    auto key = std::make_tuple(f.vh, f.nrhs, S::W, mode);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = table.find(key);
+        if (it != table.end()) return it->second;
+    }
+    std::vector<HopShape> cand;
+    const int maxnr = std::is_same<S, F64>::value ? 1 : 3;
+    for (int nr = 1; nr <= maxnr && nr <= f.nrhs; ++nr) {
+        const int ngr = (f.nrhs + nr - 1) / nr;
+        for (int gpb : {1, 2, 3, 4, 6, 12})
+            if (gpb <= ngr && (gpb == 1 || ngr % gpb == 0)) cand.push_back(HopShape{nr, gpb});
+    }
+    HopShape best{1, 1};
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    LQCD_CUDA(cudaEventCreate(&e0));
+    LQCD_CUDA(cudaEventCreate(&e1));
+    for (const HopShape &c : cand) {
+        f.gpb = c.gpb;
+        hopf_launch<S>(f, c.nr, mode, false, false, st);  // warm-up
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            LQCD_CUDA(cudaEventRecord(e0, st));
+            hopf_launch<S>(f, c.nr, mode, false, false, st);
+            LQCD_CUDA(cudaEventRecord(e1, st));
+            LQCD_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            LQCD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LQCD_CHECK_LAUNCH();
+    std::lock_guard<std::mutex> lk(mu);
+    table[key] = best;
+    tune_record(prec_name<S>(), mode, f.vh, f.nrhs, best.nr, best.gpb, best_ms);
+    return best;
+}
+
+template <class S>
+static FastHop<S> make_fast(const HopArgs<S, S, S> &a)
+{
+    FastHop<S> f{};
+    for (int m = 0; m < 4; ++m) {
+        f.L[m] = a.g.L[m];
+        f.th_re[m] = a.th_re[m];
+        f.th_im[m] = a.th_im[m];
+        if (a.th_re[m] != 1.0 || a.th_im[m] != 0.0) f.theta_mask |= 1 << m;
+    }
+    f.Lxh = a.g.Lxh;
+    f.vh = a.g.vh;
+    f.nrhs = a.nrhs;
+    f.ntiles = a.ntiles;
+    f.parity = a.parity;
+    f.dx = make_fastdiv(unsigned(a.g.Lxh));
+    f.dy = make_fastdiv(unsigned(a.g.L[1]));
+    f.dz = make_fastdiv(unsigned(a.g.L[2]));
+    f.oy = a.g.Lxh;
+    f.oz = a.g.Lxh * a.g.L[1];
+    f.ot = a.g.Lxh * a.g.L[1] * a.g.L[2];
+    f.coef = a.coef;
+    f.gpb = 1;
+    f.in = a.in;
+    f.self = a.self;
+    f.out = a.out;
+    f.U = a.U;
+    f.clov = a.clov;
+    f.gate_st = a.gate_st;
+    f.gate = a.gate;
+    f.red = a.red;
+    return f;
+}
 
 template <class S, class L, class C, int MODE, bool DAG, bool NORM>
 static void hop_go(const HopArgs<S, L, C> &a, cudaStream_t st)
@@ -40,6 +184,15 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
     double per_rhs = sb + (mode == RESID ? 0.0 : sb) + (mode == HOP_CLOV ? 0.0 : sb) + (mode == RESID ? sb : 0.0);
     double shared = 8.0 * link_bytes<L>() + (mode == SELF_PLAIN ? 0.0 : clover_bytes<C>());
     const int pi = S::W == 2 ? 0 : (S::W == 4 ? 1 : 2);
+    if (mode == HOP_CLOV || mode == SELF_CLOV) {
+        FastHop<S> f = make_fast(a);
+        const HopShape sh = hopf_tuned<S>(f, mode, st);
+        f.gpb = sh.gpb;
+        ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
+        hopf_launch<S>(f, sh.nr, mode, dag, norm, st);
+        LQCD_CHECK_LAUNCH();
+        return;
+    }
     ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
     bool ok = hop_mode<S, L, C, HOP_CLOV>(a, mode, dag, norm, st) || hop_mode<S, L, C, SELF_CLOV>(a, mode, dag, norm, st);
     if constexpr (std::is_same<S, F64>::value) {

@@ -10,6 +10,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -129,6 +130,9 @@ struct ProfScope {
     ProfScope(const char *name, double bytes, cudaStream_t st);
     ~ProfScope();
 };
+
+// records an autotuning decision (reported by lqcd_tune_report)
+void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, float ms);
 
 // algorithmic bytes per site of one field in a storage format
 template <class S> constexpr double spinor_bytes() { return S::W == 2 ? 192.0 : (S::W == 4 ? 96.0 : 52.0); }

@@ -3,6 +3,7 @@
 // pair of CUDA events brackets each launch on its own stream and the elapsed
 // times are summed when the statistics are read.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 
@@ -80,6 +81,24 @@ ProfScope::~ProfScope()
     }
 }
 
+namespace {
+std::mutex g_tune_mu;
+std::string g_tune;  // JSON objects, comma separated
+}  // namespace
+
+void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, float ms)
+{
+    static const char *modes[] = {"hopclov", "selfclov", "self", "clovsum", "resid"};
+    char buf[320];
+    std::snprintf(buf, sizeof buf,
+                  "{\"kernel\": \"hop_%s_%s\", \"sites\": %d, \"nrhs\": %d, \"rhs_per_thread\": %d, "
+                  "\"rhs_groups_per_block\": %d, \"block\": %d, \"us\": %.2f}",
+                  prec, modes[mode], vh, nrhs, nr, gpb, kBlock, ms * 1e3);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune.empty()) g_tune += ", ";
+    g_tune += buf;
+}
+
 }  // namespace lqcd
 
 using namespace lqcd;
@@ -97,6 +116,16 @@ int lqcd_profile_reset(int enable_timing)
     } catch (const Error &e) {
         return fail(e.code, e.msg);
     }
+}
+
+int lqcd_tune_report(char *buf, size_t len)
+{
+    if (!buf || len == 0) return fail(LQCD_EINVAL, "null buffer");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string j = "[" + g_tune + "]";
+    std::strncpy(buf, j.c_str(), len - 1);
+    buf[len - 1] = 0;
+    return j.size() < len ? LQCD_OK : LQCD_EINVAL;
 }
 
 int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count)

@@ -97,6 +97,7 @@ def load():
         "lqcd_serve_poll": [vp, ctypes.c_uint64, dp, ctypes.POINTER(SolveInfo), dp, ctypes.c_int],
         "lqcd_serve_destroy": [vp],
         "lqcd_profile_reset": [ctypes.c_int],
+        "lqcd_tune_report": [ctypes.c_char_p, ctypes.c_size_t],
         "lqcd_profile_read": [ctypes.POINTER(KernelStat), ctypes.c_int, ip],
     }
     for name, args in sig.items():
@@ -320,6 +321,14 @@ def profile_read() -> dict:
     return {buf[i].name.decode(): {"launches": buf[i].launches, "bytes": buf[i].bytes,
                                    "timed_launches": buf[i].timed_launches, "timed_ms": buf[i].timed_ms,
                                    "timed_bytes": buf[i].timed_bytes} for i in range(n.value)}
+
+
+def tune_report() -> list:
+    """Autotuning decisions taken so far (list of dicts)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().lqcd_tune_report(buf, len(buf)))
+    return json.loads(buf.value.decode())
 
 
 # ---------------------------------------------------------------------------
