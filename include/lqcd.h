@@ -245,6 +245,34 @@ int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count);
  * if buf is too small (the text is truncated). */
 int lqcd_tune_report(char *buf, size_t len);
 
+/* The pion contraction of lqcd_pion_contract without any device allocation,
+ * for callers that cannot allocate: processes whose device memory belongs
+ * to another allocator (a framework's caching allocator or a fixed pool,
+ * where a cudaMalloc can fail or fragment it) and loops that must not call
+ * cudaMalloc/cudaFree per call because those can synchronize the device.
+ * The paper has no counterpart: this is a library service.
+ *
+ * dims = {Lx, Ly, Lz, T} (host array, extents >= 1); prop: 12 * 24 V
+ * doubles, device memory of the current device, host layout; corr: T
+ * doubles, device memory of the current device; src_t: source time slice.
+ * No lattice handle is needed.  The work is queued on `stream` and the call
+ * returns without waiting; corr is valid once the stream reaches it.
+ *
+ * Scratch: a fixed array compiled into the library's device image (2 MiB of
+ * partial sums and 8192 counters), held by every GPU that loads the library
+ * until the process exits.  The lattice must satisfy
+ * T * ceil(12 V / (512 T)) <= 262144 and T <= 8192 (32^3 x 64 needs
+ * 49152); larger lattices get LQCD_EINVAL with the counts
+ * in the message (use lqcd_pion_contract there).  The first call on a
+ * device looks up the device address of the array (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture on that
+ * device.  Every call shares the array, and the counters are cleared at the
+ * start of each call: calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong results, so serialize them.
+ * Errors: LQCD_EINVAL (null pointer, bad extent or source, too large),
+ * LQCD_ECUDA. */
+int lqcd_pion_contract_noalloc(const int dims[4], const double *prop, int src_t, double *corr, void *stream);
+
 /* ---------------- serving loop (continuous batching) ------------------- */
 
 /* A server owns one device thread that admits propagator requests

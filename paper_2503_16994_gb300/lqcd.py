@@ -90,6 +90,7 @@ def load():
         "lqcd_pion_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip, vp, vp,
                            ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
         "lqcd_pion_contract": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp],
+        "lqcd_pion_contract_noalloc": [ip, vp, ctypes.c_int, vp, vp],
         "lqcd_serve_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)],
         "lqcd_serve_gauge": [vp, ip, vp, ip],
         "lqcd_serve_submit": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip,
@@ -302,6 +303,21 @@ def pion_contract(lat, prop, src_t, T=None, corr=None, stream=None):
     _check(load().lqcd_pion_contract(lat, p.ctypes.data_as(ctypes.c_void_p), int(src_t),
                                      c.ctypes.data_as(ctypes.c_void_p), 0, None))
     return c
+
+
+def pion_contract_noalloc(dims, prop, src_t, corr, stream=None):
+    """C(t) into the float64 CUDA tensor `corr` from a CUDA tensor `prop`, allocating nothing.
+
+    For callers that cannot allocate device memory (see lqcd.h).  The work is
+    queued on the stream; synchronize before reading `corr`.
+    """
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    n = prop.numel() * (2 if prop.is_complex() else 1)
+    if corr.numel() != int(dims[3]) or str(corr.dtype) != "torch.float64" or not corr.is_cuda:
+        raise ValueError("corr must be a float64 CUDA tensor of length T")
+    _check(load().lqcd_pion_contract_noalloc(d, _dev_ptr(prop, 12 * 24 * int(np.prod(dims))), int(src_t),
+                                             ctypes.c_void_p(corr.data_ptr()), _stream_of(prop, stream)))
+    return corr
 
 
 # ---------------------------------------------------------------------------
