@@ -260,6 +260,65 @@ def run_dslash_only(args):
 
 
 # ---------------------------------------------------------------------------
+# serving: a Poisson stream of propagator requests of mixed sizes
+# ---------------------------------------------------------------------------
+SERVE = {"sizes": [[8, 8, 8, 16], [16, 16, 16, 32], [24, 24, 24, 48], [32, 32, 32, 64]], "fields_per_size": 2,
+         "eps": 0.4, "csw": 1.5, "kappa": [0.120, 0.134], "rate": 20.0, "slots": 4, "precision": "fp16",
+         "tol": 1e-10, "seed": 7}
+
+
+def serving_measure(lqcd, n_requests, rate=None):
+    """Submits n_requests at Poisson arrival times (seeded) to lqcd_serve_*.
+
+    Sizes uniform over SERVE['sizes'], kappa uniform in SERVE['kappa'], 8
+    resident gauge fields (2 per size).  Latency = finish - arrival.  Service
+    time = finish - start of each request (it overlaps with others on the
+    device).  Offered load rho = rate x mean service time."""
+    from paper_2503_16994_gb300 import inputs
+    rate = rate or SERVE["rate"]
+    srv = lqcd.serve_create(device=0, hbm_budget_bytes=0, max_slots=SERVE["slots"])
+    try:
+        gids = []
+        for si, dims in enumerate(SERVE["sizes"]):
+            for f in range(SERVE["fields_per_size"]):
+                U = inputs.gauge_field(dims, SERVE["eps"], seed=100 + 10 * si + f, workers=None)
+                gids.append((lqcd.serve_gauge(srv, dims, U), dims))
+        seed = SERVE["seed"]
+        gaps = inputs.exponential_gaps(seed, n_requests, rate)
+        pick = (inputs.uniforms(seed + 1, 0, n_requests) * len(gids)).astype(int)
+        kap = inputs.kappa_values(seed + 2, n_requests, *SERVE["kappa"])
+        sp = lqcd.solver_params(tol=SERVE["tol"], maxiter=20000, precision=SERVE["precision"])
+        t0 = time.perf_counter()
+        arrivals = np.cumsum(gaps)
+        tickets = []
+        for k in range(n_requests):
+            dt = arrivals[k] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            g, dims = gids[pick[k]]
+            tickets.append((lqcd.serve_submit(srv, g, lqcd.dirac_params(float(kap[k]), SERVE["csw"]), sp,
+                                              (0, 0, 0, 0)), dims))
+        lat, svc, ok = [], [], 0
+        first, last = None, None
+        for t, dims in tickets:
+            rc, corr, infos, ts = lqcd.serve_poll(srv, t, dims[3], timeout_ms=-1)
+            ok += rc == lqcd.OK
+            lat.append(ts[3] - ts[0])
+            svc.append(ts[3] - ts[2])
+            first = ts[0] if first is None else min(first, ts[0])
+            last = ts[3] if last is None else max(last, ts[3])
+    finally:
+        lqcd.serve_destroy(srv)
+    lat = np.array(lat)
+    return {"requests": n_requests, "converged": int(ok), "rate_per_s": rate, "slots": SERVE["slots"],
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_service_s": float(np.mean(svc)), "offered_load_rho": float(rate * np.mean(svc) / SERVE["slots"]),
+            "solves_per_s": 12 * n_requests / (last - first), "makespan_s": last - first,
+            "workload": "Poisson arrivals, sizes {8^3x16,16^3x32,24^3x48,32^3x64}, 8 resident fields eps 0.4, "
+                        "kappa U[0.120,0.134], csw 1.5, 12 RHS FP16 mixed, tol 1e-10"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -382,6 +441,7 @@ def run_ours(args):
                 "true_resid_max": max(i["true_resid"] for i in infos64)}
 
     dslash = None if args.no_dslash else dslash_measure(lqcd, lat, gid, dp, dims)
+    serving = None if (args.serve_requests <= 0 or rank != 0) else serving_measure(lqcd, args.serve_requests)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -400,7 +460,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": None, "kernel": "hop_f16_* (hopclov + selfclov)",
                          "peak_source": f"{peak_kind} hbm_gbs", "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS,
                          "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None},
-            "dslash": dslash, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "dslash": dslash, "serving": serving, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
             "fp64_gpu": fp64, "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
             "iters": {"inner_max": max(i["iters_inner"] for i in infos_last),
                       "outer_max": max(i["iters_outer"] for i in infos_last),
@@ -456,6 +516,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
     ap.add_argument("--dslash-only", action="store_true", help="time only the Dslash on --lattice")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--precision", default="fp16")

@@ -273,12 +273,23 @@ __global__ void clover_convert_kernel(long vh, long stride, const double2 *src, 
     }
 }
 
-CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st)
+size_t clover_bytes(const lqcd_lattice_s *lat)
+{
+    return 2 * 2 * (size_t)lat->stride * (36 * sizeof(double2) + 18 * sizeof(float4) + 9 * sizeof(uint4));
+}
+
+size_t gauge_bytes(const lqcd_lattice_s *lat)
+{
+    return 2 * 4 * (size_t)lat->stride * (9 * sizeof(double2) + 3 * sizeof(float4) + sizeof(uint4) + sizeof(uint2));
+}
+
+std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st,
+                                        bool async)
 {
     const double kc = kappa * csw;
-    auto it = g.clover.find(kc);
-    if (it != g.clover.end()) return *it->second;
     auto c = std::make_unique<CloverSet>();
+    if (async)
+        for (DevBuf *b : {&c->a64, &c->ainv64, &c->a32, &c->ainv32, &c->a16, &c->ainv16}) b->set_async(st);
     const long S = lat->stride;
     c->a64.ensure(sizeof(double2) * 2 * 36 * S);
     c->ainv64.ensure(sizeof(double2) * 2 * 36 * S);
@@ -297,6 +308,15 @@ CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw
     clover_convert_kernel<<<g2, kBlock, 0, st>>>(lat->vh, S, c->ainv64.as<const double2>(), c->ainv32.as<float4>(),
                                                  c->ainv16.as<uint4>());
     LQCD_CHECK_LAUNCH();
+    return c;
+}
+
+CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st)
+{
+    const double kc = kappa * csw;
+    auto it = g.clover.find(kc);
+    if (it != g.clover.end()) return *it->second;
+    auto c = clover_build(lat, g, kappa, csw, st, false);
     CloverSet &ref = *c;
     g.clover.emplace(kc, std::move(c));
     return ref;
@@ -438,20 +458,15 @@ __global__ void __launch_bounds__(128) contract_aos_kernel(long V, long v3, int 
     slice_finish(acc, t, c, nchunk, T, src_t, partial, counter, corr);
 }
 
+// partial: T * ceil(V3/2 / 128) doubles; counter: T zeroed counters (left zeroed)
 void pion_contract_soa(lqcd_lattice_s *lat, SpinorField<F64> even, SpinorField<F64> odd, int src_t,
-                       double *corr_dev, cudaStream_t st)
+                       double *corr_dev, double *partial, unsigned *counter, cudaStream_t st)
 {
     const int T = lat->dims[3];
     const long v3h = lat->vh / T;
     const int nchunk = int((v3h + kBlock - 1) / kBlock);
-    lat->red_partial.ensure(sizeof(double) * (size_t)T * nchunk);
-    if (lat->red_counter.bytes < sizeof(unsigned) * 4096) {
-        lat->red_counter.ensure(sizeof(unsigned) * 4096);
-        LQCD_CUDA(cudaMemsetAsync(lat->red_counter.p, 0, lat->red_counter.bytes, st));
-    }
     ProfScope prof("pion_contract", double(lat->V) * 12 * 192.0, st);
-    contract_soa_kernel<<<dim3(nchunk, T), kBlock, 0, st>>>(v3h, T, src_t, even, odd, lat->red_partial.as<double>(),
-                                                           lat->red_counter.as<unsigned>(), corr_dev);
+    contract_soa_kernel<<<dim3(nchunk, T), kBlock, 0, st>>>(v3h, T, src_t, even, odd, partial, counter, corr_dev);
     LQCD_CHECK_LAUNCH();
 }
 

@@ -46,13 +46,20 @@ int fail(int code, const std::string &msg);
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t async_st = nullptr;  // set: stream-ordered allocation (cudaMallocAsync / cudaFreeAsync)
+    bool async = false;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            if (async)
+                cudaFreeAsync(p, async_st);
+            else
+                cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
     }
@@ -61,8 +68,17 @@ struct DevBuf {
     {
         if (bytes >= n) return;
         release();
-        LQCD_CUDA(cudaMalloc(&p, n));
+        if (async)
+            LQCD_CUDA(cudaMallocAsync(&p, n, async_st));
+        else
+            LQCD_CUDA(cudaMalloc(&p, n));
         bytes = n;
+    }
+    // later allocations of this buffer are stream-ordered on `st` (no device-wide synchronisation)
+    void set_async(cudaStream_t st)
+    {
+        async = true;
+        async_st = st;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
@@ -96,9 +112,21 @@ struct Workspace {
     DevBuf e;                                    // correction (FP32, or FP64 for the FP64 solver)
     DevBuf state;                                // RhsState[nrhs]
     DevBuf partial, counter;                     // reductions
-    RhsState *host_state = nullptr;              // pinned mirror
+    RhsState *host_state = nullptr;              // host mirror (pinned unless host_pageable)
+    bool host_pageable = false;
     ~Workspace();
 };
+
+// Solver workspace for (nrhs, precision) on a lattice.  async: the device
+// buffers are stream-ordered allocations on `st` (used by the server, whose
+// requests come and go while other streams run) and the host mirror is
+// pageable memory.
+std::unique_ptr<Workspace> workspace_build(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_t st, bool async);
+size_t workspace_bytes(const lqcd_lattice_s *lat, int nrhs, int prec);
+std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st,
+                                        bool async);
+size_t clover_bytes(const lqcd_lattice_s *lat);
+size_t gauge_bytes(const lqcd_lattice_s *lat);
 
 }  // namespace lqcd
 
@@ -157,7 +185,7 @@ void point_sources(lqcd_lattice_s *lat, const int src[4], SpinorField<F64> even,
                    cudaStream_t st);
 // corr[t] (device, T doubles) from 12 FP64 SoA columns, t relative to src_t
 void pion_contract_soa(lqcd_lattice_s *lat, SpinorField<F64> even, SpinorField<F64> odd, int src_t,
-                       double *corr_dev, cudaStream_t st);
+                       double *corr_dev, double *partial, unsigned *counter, cudaStream_t st);
 // corr[t] from 12 host-layout columns already on the device
 void pion_contract_aos(lqcd_lattice_s *lat, const double *prop_dev, int src_t, double *corr_dev,
                        double *partial, unsigned *counter, cudaStream_t st);
@@ -193,5 +221,10 @@ void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
 int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,
           const double *b_dev, double *x_dev, const int *src, int nrhs, lqcd_solve_info *info, double *corr_dev,
           cudaStream_t st);
+// The same on explicit clover fields and workspace (no lattice caches); stops
+// early when *cancel becomes true (then returns nrhs).
+int solve_on(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,
+             const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
+             lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel);
 
 }  // namespace lqcd

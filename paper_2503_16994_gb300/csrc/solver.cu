@@ -21,6 +21,7 @@
 // few iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "lqcd_impl.h"
 
@@ -38,7 +39,80 @@ template <class S> static SpinorField<S> fld(DevBuf &b, DevBuf *sc, long stride)
 
 Workspace::~Workspace()
 {
-    if (host_state) cudaFreeHost(host_state);
+    if (host_state) {
+        if (host_pageable)
+            std::free(host_state);
+        else
+            cudaFreeHost(host_state);
+    }
+}
+
+// partial sums: the solver's reductions need nrhs * ntiles, the contraction
+// T * ceil(V3/2 / 128) <= ntiles + T; counters: max(nrhs, T)
+static size_t partial_count(const lqcd_lattice_s *lat, int nrhs)
+{
+    return std::max((size_t)nrhs * ntiles_of(lat->vh), (size_t)ntiles_of(lat->vh) + lat->dims[3]);
+}
+
+template <class W, class E>
+static size_t workspace_bytes_t(const lqcd_lattice_s *lat, int nrhs)
+{
+    const long S = lat->stride;
+    size_t b = 7 * field_bytes<F64>(S, nrhs) + 5 * field_bytes<W>(S, nrhs) + field_bytes<E>(S, nrhs);
+    if (std::is_same<W, F16>::value) b += 5 * sizeof(float) * S * nrhs;
+    b += sizeof(RhsState) * nrhs + sizeof(double) * partial_count(lat, nrhs) +
+         sizeof(unsigned) * std::max(nrhs, lat->dims[3]);
+    return b;
+}
+
+size_t workspace_bytes(const lqcd_lattice_s *lat, int nrhs, int prec)
+{
+    switch (prec) {
+    case LQCD_PREC_FP64: return workspace_bytes_t<F64, F64>(lat, nrhs);
+    case LQCD_PREC_MIXED_FP32: return workspace_bytes_t<F32, F32>(lat, nrhs);
+    default: return workspace_bytes_t<F16, F32>(lat, nrhs);
+    }
+}
+
+template <class W, class E>
+static std::unique_ptr<Workspace> workspace_build_t(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_t st,
+                                                    bool async)
+{
+    auto w = std::make_unique<Workspace>();
+    w->nrhs = nrhs;
+    w->prec = prec;
+    if (async)
+        for (DevBuf *b : {&w->b_e, &w->b_o, &w->bhat, &w->x_e, &w->x_o, &w->t64, &w->w64, &w->p, &w->t, &w->w, &w->r,
+                          &w->z, &w->p_sc, &w->t_sc, &w->w_sc, &w->r_sc, &w->z_sc, &w->e, &w->state, &w->partial,
+                          &w->counter})
+            b->set_async(st);
+    const long S = lat->stride;
+    for (DevBuf *b : {&w->b_e, &w->b_o, &w->bhat, &w->x_e, &w->x_o, &w->t64, &w->w64}) b->ensure(field_bytes<F64>(S, nrhs));
+    for (DevBuf *b : {&w->p, &w->t, &w->w, &w->r, &w->z}) b->ensure(field_bytes<W>(S, nrhs));
+    if (std::is_same<W, F16>::value)
+        for (DevBuf *b : {&w->p_sc, &w->t_sc, &w->w_sc, &w->r_sc, &w->z_sc}) b->ensure(sizeof(float) * S * nrhs);
+    w->e.ensure(field_bytes<E>(S, nrhs));
+    w->state.ensure(sizeof(RhsState) * nrhs);
+    w->partial.ensure(sizeof(double) * partial_count(lat, nrhs));
+    w->counter.ensure(sizeof(unsigned) * std::max(nrhs, lat->dims[3]));
+    LQCD_CUDA(cudaMemsetAsync(w->counter.p, 0, w->counter.bytes, st));
+    if (async) {
+        w->host_pageable = true;
+        w->host_state = static_cast<RhsState *>(std::malloc(sizeof(RhsState) * nrhs));
+        if (!w->host_state) throw Error{LQCD_ENOMEM, "host allocation failed"};
+    } else {
+        LQCD_CUDA(cudaMallocHost(&w->host_state, sizeof(RhsState) * nrhs));
+    }
+    return w;
+}
+
+std::unique_ptr<Workspace> workspace_build(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_t st, bool async)
+{
+    switch (prec) {
+    case LQCD_PREC_FP64: return workspace_build_t<F64, F64>(lat, nrhs, prec, st, async);
+    case LQCD_PREC_MIXED_FP32: return workspace_build_t<F32, F32>(lat, nrhs, prec, st, async);
+    default: return workspace_build_t<F16, F32>(lat, nrhs, prec, st, async);
+    }
 }
 
 template <class W, class E>
@@ -47,20 +121,7 @@ static Workspace &workspace(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_
     auto key = std::make_pair(nrhs, prec);
     auto it = lat->ws.find(key);
     if (it != lat->ws.end()) return *it->second;
-    auto w = std::make_unique<Workspace>();
-    w->nrhs = nrhs;
-    w->prec = prec;
-    const long S = lat->stride;
-    for (DevBuf *b : {&w->b_e, &w->b_o, &w->bhat, &w->x_e, &w->x_o, &w->t64, &w->w64}) b->ensure(field_bytes<F64>(S, nrhs));
-    for (DevBuf *b : {&w->p, &w->t, &w->w, &w->r, &w->z}) b->ensure(field_bytes<W>(S, nrhs));
-    if (std::is_same<W, F16>::value)
-        for (DevBuf *b : {&w->p_sc, &w->t_sc, &w->w_sc, &w->r_sc, &w->z_sc}) b->ensure(sizeof(float) * S * nrhs);
-    w->e.ensure(field_bytes<E>(S, nrhs));
-    w->state.ensure(sizeof(RhsState) * nrhs);
-    w->partial.ensure(sizeof(double) * (size_t)nrhs * ntiles_of(lat->vh));
-    w->counter.ensure(sizeof(unsigned) * nrhs);
-    LQCD_CUDA(cudaMemsetAsync(w->counter.p, 0, w->counter.bytes, st));
-    LQCD_CUDA(cudaMallocHost(&w->host_state, sizeof(RhsState) * nrhs));
+    auto w = workspace_build_t<W, E>(lat, nrhs, prec, st, false);
     Workspace &ref = *w;
     lat->ws.emplace(key, std::move(w));
     return ref;
@@ -325,6 +386,8 @@ struct Solver {
         return true;
     }
 
+    const volatile bool *cancel = nullptr;  // set by the server: stop at the next poll
+
     // returns the number of RHS that did not reach tol
     int run(const lqcd_solver_params &sp, lqcd_solve_info *info)
     {
@@ -343,7 +406,7 @@ struct Solver {
         for (int attempt = 0; attempt < 4; ++attempt) {
             long guard = (long)sp.maxiter + 64;
             bool finished = false;
-            for (long it = 0; it < guard && !finished; it += chunk) {
+            for (long it = 0; it < guard && !finished && !(cancel && *cancel); it += chunk) {
                 for (int k = 0; k < chunk; ++k) {
                     half1();
                     if (poll_each) {
@@ -375,7 +438,7 @@ struct Solver {
                     retry = true;
                 }
             }
-            if (!retry) break;
+            if (!retry || (cancel && *cancel)) break;
             push_states();
             reliable_update();
             half2();
@@ -398,21 +461,47 @@ struct Solver {
 };
 
 template <class W, class E>
-static int solve_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, const lqcd_dirac_params &dp,
+static int solve_on_t(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,
                       const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
-                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st)
+                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel)
 {
-    Workspace &ws = workspace<W, E>(lat, nrhs, sp.precision, st);
     Solver<W, E> s(lat, ws, g, cl, dp, nrhs, st);
+    s.cancel = cancel;
     if (src)
         point_sources(lat, src, s.b_e, s.b_o, st);
     else
         spinor_to_soa(lat, b_dev, nrhs, s.b_e, s.b_o, st);
     int failed = s.run(sp, info);
+    if (cancel && *cancel) failed = nrhs;
     if (x_dev) spinor_from_soa(lat, x_dev, nrhs, s.x_e, s.x_o, st);
-    if (corr_dev) pion_contract_soa(lat, s.x_e, s.x_o, src[3], corr_dev, st);
+    if (corr_dev)
+        pion_contract_soa(lat, s.x_e, s.x_o, src[3], corr_dev, ws.partial.as<double>(), ws.counter.as<unsigned>(), st);
     LQCD_CUDA(cudaStreamSynchronize(st));
     return failed;
+}
+
+int solve_on(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,
+             const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
+             lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel)
+{
+    switch (sp.precision) {
+    case LQCD_PREC_FP64:
+        return solve_on_t<F64, F64>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel);
+    case LQCD_PREC_MIXED_FP32:
+        return solve_on_t<F32, F32>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel);
+    case LQCD_PREC_MIXED_FP16:
+        return solve_on_t<F16, F32>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel);
+    default: throw Error{LQCD_EINVAL, "unknown precision"};
+    }
+}
+
+template <class W, class E>
+static int solve_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, const lqcd_dirac_params &dp,
+                      const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
+                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st)
+{
+    Workspace &ws = workspace<W, E>(lat, nrhs, sp.precision, st);
+    return solve_on_t<W, E>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, nullptr);
 }
 
 void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
