@@ -256,7 +256,7 @@ def run_dslash_only(args):
     legs = [(args.precision, args.nrhs, args.repeat)]
     res = dslash_measure(lqcd, lat, gid, dp, dims, legs)
     lqcd.lattice_destroy(lat)
-    print(json.dumps({"dslash": res, "lattice": list(dims)}))
+    print(json.dumps({"dslash": res, "lattice": list(dims), "tuning": lqcd.tune_report()}))
 
 
 # ---------------------------------------------------------------------------
@@ -466,6 +466,7 @@ def run_ours(args):
                       "outer_max": max(i["iters_outer"] for i in infos_last),
                       "true_resid_max": max(i["true_resid"] for i in infos_last)},
             "kernels": per_kernel,
+            "tuning": lqcd.tune_report(),
         }
         print(json.dumps(out))
     lqcd.lattice_destroy(lat)

@@ -238,10 +238,15 @@ int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count);
 /* Autotuning decisions taken so far in this process, as a JSON array
  * written into buf (len bytes, NUL-terminated).  Each entry names a kernel,
  * the problem (sites per parity, right-hand sides) and the chosen shape
- * (right-hand sides per thread, threads per block) with its time.  The
- * hopping kernels of the FP32/FP16 formats time 1..4 right-hand sides per
- * thread on their first launch for each problem and keep the fastest
- * (environment variable LQCD_HOP_NR forces a value).  Returns LQCD_EINVAL
+ * with its time: rhs_per_thread (1..3: right-hand sides per thread in
+ * scalar arithmetic; 0: two right-hand sides in the lanes of packed FP32x2
+ * instructions; -2/-4/-8: one right-hand side with the loads of 2/4/8
+ * directions issued ahead), rhs_groups_per_block (groups run in sequence by
+ * one block), min_blocks_per_sm (register cap), tiles_per_supertile (block
+ * order) and block (threads).  The hopping kernels time these candidates on
+ * their first launch for each (sites, nrhs, format, mode) and keep the
+ * fastest; the environment variables LQCD_HOP_NR, LQCD_HOP_GPB,
+ * LQCD_HOP_MINB and LQCD_HOP_SWZ force a shape instead.  Returns LQCD_EINVAL
  * if buf is too small (the text is truncated). */
 int lqcd_tune_report(char *buf, size_t len);
 

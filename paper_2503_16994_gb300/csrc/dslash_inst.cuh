@@ -16,12 +16,22 @@ inline FastDiv make_fastdiv(unsigned d)
     return FastDiv{d, unsigned(m), l};
 }
 
+template <class S>
+static long padded_tiles(const FastHop<S> &f)
+{
+    return long((f.ntiles + f.swz - 1) / f.swz) * f.swz;
+}
+
 template <class S, int NR, int MODE, bool DAG, bool NORM>
 static void hopf_go(const FastHop<S> &f, cudaStream_t st)
 {
     const int ngr = (f.nrhs + NR - 1) / NR;
-    const unsigned grid = unsigned(f.ntiles * ((ngr + f.gpb - 1) / f.gpb));
-    hopf_kernel<S, NR, MODE, DAG, NORM><<<grid, kBlock, 0, st>>>(f);
+    const unsigned grid = unsigned(padded_tiles(f) * ((ngr + f.gpb - 1) / f.gpb));
+    // minimum resident blocks per SM (register cap) as chosen by the autotuner
+    if (NR == 1 && f.minb >= 6)
+        hopf_kernel<S, NR, MODE, DAG, NORM, 6><<<grid, kBlock, 0, st>>>(f);
+    else
+        hopf_kernel<S, NR, MODE, DAG, NORM, 1><<<grid, kBlock, 0, st>>>(f);
 }
 
 template <class S, int NR>
@@ -36,9 +46,67 @@ static void hopf_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cu
     }
 }
 
+template <class S, int MODE, bool DAG, bool NORM>
+static void hopp_go(const FastHop<S> &f, cudaStream_t st)
+{
+    const int ngr = (f.nrhs + 1) / 2;
+    const unsigned grid = unsigned(padded_tiles(f) * ((ngr + f.gpb - 1) / f.gpb));
+    if (f.minb >= 4)
+        hopp_kernel<S, MODE, DAG, NORM, 4><<<grid, kBlock, 0, st>>>(f);
+    else
+        hopp_kernel<S, MODE, DAG, NORM, 1><<<grid, kBlock, 0, st>>>(f);
+}
+
+template <class S>
+static void hopp_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st)
+{
+    if (mode == HOP_CLOV) {
+        if (dag) norm ? hopp_go<S, HOP_CLOV, true, true>(f, st) : hopp_go<S, HOP_CLOV, true, false>(f, st);
+        else norm ? hopp_go<S, HOP_CLOV, false, true>(f, st) : hopp_go<S, HOP_CLOV, false, false>(f, st);
+    } else {
+        if (dag) norm ? hopp_go<S, SELF_CLOV, true, true>(f, st) : hopp_go<S, SELF_CLOV, true, false>(f, st);
+        else norm ? hopp_go<S, SELF_CLOV, false, true>(f, st) : hopp_go<S, SELF_CLOV, false, false>(f, st);
+    }
+}
+
+template <class S, int MODE, bool DAG, bool NORM>
+static void hopq_go(const FastHop<S> &f, int pf, cudaStream_t st)
+{
+    const unsigned grid = unsigned(padded_tiles(f) * ((f.nrhs + f.gpb - 1) / f.gpb));
+    if (pf == 8) hopq_kernel<S, MODE, DAG, NORM, 8><<<grid, kBlock, 0, st>>>(f);
+    else if (pf == 4) hopq_kernel<S, MODE, DAG, NORM, 4><<<grid, kBlock, 0, st>>>(f);
+    else hopq_kernel<S, MODE, DAG, NORM, 2><<<grid, kBlock, 0, st>>>(f);
+}
+
+template <class S>
+static void hopq_dispatch(const FastHop<S> &f, int pf, int mode, bool dag, bool norm, cudaStream_t st)
+{
+    if (mode == HOP_CLOV) {
+        if (dag) norm ? hopq_go<S, HOP_CLOV, true, true>(f, pf, st) : hopq_go<S, HOP_CLOV, true, false>(f, pf, st);
+        else norm ? hopq_go<S, HOP_CLOV, false, true>(f, pf, st) : hopq_go<S, HOP_CLOV, false, false>(f, pf, st);
+    } else {
+        if (dag) norm ? hopq_go<S, SELF_CLOV, true, true>(f, pf, st) : hopq_go<S, SELF_CLOV, true, false>(f, pf, st);
+        else norm ? hopq_go<S, SELF_CLOV, false, true>(f, pf, st) : hopq_go<S, SELF_CLOV, false, false>(f, pf, st);
+    }
+}
+
+// nr in 1..3: NR right-hand sides per thread in scalar FP32/FP64 arithmetic;
+// nr == 0: two right-hand sides per thread in the lanes of packed FP32x2;
+// nr == -2, -4, -8: one right-hand side per thread, loads of 2, 4 or 8
+// directions issued before their arithmetic (FP16/FP32 only)
 template <class S>
 static void hopf_launch(const FastHop<S> &f, int nr, int mode, bool dag, bool norm, cudaStream_t st)
 {
+    if constexpr (!std::is_same<S, F64>::value) {
+        if (nr == 0) {
+            hopp_dispatch<S>(f, mode, dag, norm, st);
+            return;
+        }
+        if (nr < 0) {
+            hopq_dispatch<S>(f, -nr, mode, dag, norm, st);
+            return;
+        }
+    }
     if constexpr (std::is_same<S, F64>::value) {
         hopf_dispatch<S, 1>(f, mode, dag, norm, st);
     } else {
@@ -56,7 +124,7 @@ static void hopf_launch(const FastHop<S> &f, int nr, int mode, bool dag, bool no
 // candidate writes the output the real launch then overwrites) and keeps
 // the fastest.  LQCD_HOP_NR / LQCD_HOP_GPB force a value.
 struct HopShape {
-    int nr, gpb;
+    int nr, gpb, minb, swz;
 };
 
 template <class S>
@@ -68,7 +136,10 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
     const char *env_gpb = std::getenv("LQCD_HOP_GPB");
     if (env_nr || env_gpb) {
         int nr = env_nr ? std::atoi(env_nr) : 1, gpb = env_gpb ? std::atoi(env_gpb) : 1;
-        return HopShape{std::min(std::max(nr, 1), 4), std::max(gpb, 1)};
+        if (std::is_same<S, F64>::value || (nr != -2 && nr != -4 && nr != -8 && (nr < 0 || nr > 3))) nr = 1;
+        const char *env_mb = std::getenv("LQCD_HOP_MINB");
+        const char *env_sw = std::getenv("LQCD_HOP_SWZ");
+        return HopShape{nr, std::max(gpb, 1), env_mb ? std::atoi(env_mb) : 1, env_sw ? std::max(1, std::atoi(env_sw)) : 1};
     }
     auto key = std::make_tuple(f.vh, f.nrhs, S::W, mode);
     {
@@ -78,18 +149,32 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
     }
     std::vector<HopShape> cand;
     const int maxnr = std::is_same<S, F64>::value ? 1 : 3;
-    for (int nr = 1; nr <= maxnr && nr <= f.nrhs; ++nr) {
-        const int ngr = (f.nrhs + nr - 1) / nr;
+    for (int nr = (std::is_same<S, F64>::value || f.nrhs < 2) ? 1 : 0; nr <= maxnr && nr <= f.nrhs; ++nr) {
+        const int per = nr == 0 ? 2 : nr;
+        const int ngr = (f.nrhs + per - 1) / per;
         for (int gpb : {1, 2, 3, 4, 6, 12})
-            if (gpb <= ngr && (gpb == 1 || ngr % gpb == 0)) cand.push_back(HopShape{nr, gpb});
+            if (gpb <= ngr && (gpb == 1 || ngr % gpb == 0)) {
+                for (int swz : {1, 8, 32}) {
+                    if (swz > 1 && ngr / gpb < 2) continue;  // one block per tile: order is irrelevant
+                    cand.push_back(HopShape{nr, gpb, 1, swz});
+                }
+                if (!std::is_same<S, F64>::value && nr == 1) cand.push_back(HopShape{nr, gpb, 6, 1});
+                if (nr == 0) cand.push_back(HopShape{nr, gpb, 4, 1});
+            }
     }
-    HopShape best{1, 1};
+    if (!std::is_same<S, F64>::value)
+        for (int pf : {2, 4, 8})
+            for (int gpb : {1, 2, 3})
+                if (gpb <= f.nrhs && (gpb == 1 || f.nrhs % gpb == 0)) cand.push_back(HopShape{-pf, gpb, 1, 1});
+    HopShape best{1, 1, 1, 1};
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     LQCD_CUDA(cudaEventCreate(&e0));
     LQCD_CUDA(cudaEventCreate(&e1));
     for (const HopShape &c : cand) {
         f.gpb = c.gpb;
+        f.minb = c.minb;
+        f.swz = c.swz;
         hopf_launch<S>(f, c.nr, mode, false, false, st);  // warm-up
         float ms_min = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -111,7 +196,7 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
     LQCD_CHECK_LAUNCH();
     std::lock_guard<std::mutex> lk(mu);
     table[key] = best;
-    tune_record(prec_name<S>(), mode, f.vh, f.nrhs, best.nr, best.gpb, best_ms);
+    tune_record(prec_name<S>(), mode, f.vh, f.nrhs, best.nr, best.gpb, best.minb, best.swz, best_ms);
     return best;
 }
 
@@ -138,6 +223,8 @@ static FastHop<S> make_fast(const HopArgs<S, S, S> &a)
     f.ot = a.g.Lxh * a.g.L[1] * a.g.L[2];
     f.coef = a.coef;
     f.gpb = 1;
+    f.minb = 1;
+    f.swz = 1;
     f.in = a.in;
     f.self = a.self;
     f.out = a.out;
@@ -188,6 +275,8 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
         FastHop<S> f = make_fast(a);
         const HopShape sh = hopf_tuned<S>(f, mode, st);
         f.gpb = sh.gpb;
+        f.minb = sh.minb;
+        f.swz = sh.swz;
         ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
         hopf_launch<S>(f, sh.nr, mode, dag, norm, st);
         LQCD_CHECK_LAUNCH();

@@ -34,6 +34,8 @@ struct FastHop {
     double coef;
     double th_re[4], th_im[4];
     int gpb;                     // groups of NR right-hand sides per block
+    int minb;                    // register cap: minimum resident blocks per SM (1, 4 or 6)
+    int swz;                     // tiles per super-tile in the block order (1: tile-major)
     int theta_mask;              // bit mu set: theta_mu != 1
     SpinorField<S> in, self, out;
     LinkField<S> U;
@@ -502,17 +504,570 @@ __device__ __forceinline__ void hopf_group(const FastHop<S> &a, int tile, int g)
     }
 }
 
-// Block b handles tile b / nbt and groups [(b % nbt) gpb, ... + gpb) of NR
-// right-hand sides, nbt = ceil(groups / gpb); groups run one after another.
-template <class S, int NR, int MODE, bool DAG, bool NORM>
-__global__ void __launch_bounds__(128) hopf_kernel(const FastHop<S> a)
+// Block order: blocks are grouped in super-tiles of swz consecutive tiles;
+// inside a super-tile the blocks run tile-fastest for each block-of-groups
+// index, so neighbouring blocks work on neighbouring tiles of the same
+// right-hand sides while a super-tile's links and clover stay in L2 for all
+// right-hand sides.  swz = 1 puts the blocks of one tile next to each other.
+// Returns false for the padding blocks of the last super-tile.
+__device__ __forceinline__ bool block_tile(int ntiles, int nbt, int swz, int &tile, int &gb)
+{
+    const int per_super = swz * nbt;
+    const int super = blockIdx.x / per_super, rem = blockIdx.x - super * per_super;
+    gb = rem / swz;
+    tile = super * swz + (rem - gb * swz);
+    return tile < ntiles;
+}
+
+// Block handles one tile and groups [gb gpb, gb gpb + gpb) of NR right-hand
+// sides, nbt = ceil(groups / gpb) blocks per tile; groups run in sequence.
+template <class S, int NR, int MODE, bool DAG, bool NORM, int MINB>
+__global__ void __launch_bounds__(128, MINB) hopf_kernel(const FastHop<S> a)
 {
     const int ngr = (a.nrhs + NR - 1) / NR;
     const int nbt = (ngr + a.gpb - 1) / a.gpb;
-    const int tile = blockIdx.x / nbt;
-    const int g0 = (blockIdx.x % nbt) * a.gpb;
+    int tile, gb;
+    if (!block_tile(a.ntiles, nbt, a.swz, tile, gb)) return;
+    const int g0 = gb * a.gpb;
     const int g1 = min(ngr, g0 + a.gpb);
     for (int g = g0; g < g1; ++g) hopf_group<S, NR, MODE, DAG, NORM>(a, tile, g);
+}
+
+// ---------------------------------------------------------------------------
+// Paired variant (FP16 / FP32 storage): two right-hand sides ride in the two
+// lanes of a float2 and every arithmetic step is one packed FP32x2
+// instruction (FFMA2 / FADD2 / FMUL2, sm_100 and later) for both.  Link and
+// clover entries are shared by the two lanes (broadcast); the spin
+// projection and the i sigma shuffles never cross lanes.
+// ---------------------------------------------------------------------------
+struct cp {
+    float2 r, i;
+};
+
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// a + s b for a compile-time sign s
+template <int SGN> __device__ __forceinline__ float2 p_addsg(float2 a, float2 b)
+{
+    if constexpr (SGN > 0) return p_add(a, b);
+    else return p_sub(a, b);
+}
+
+// the 24 reals of right-hand sides ja (lane x) and jb (lane y) at site y;
+// FP16 values unscaled, the per-site scales returned as a pair
+template <class S>
+__device__ __forceinline__ float2 load_pair(const SpinorField<S> &f, int ja, int jb, int y, cp v[12])
+{
+    constexpr int NP = spinor_planes<S>::n;
+    const typename S::word *ba = f.p + (long)ja * NP * f.stride + y;
+    const typename S::word *bb = f.p + (long)jb * NP * f.stride + y;
+    if constexpr (S::W == 4) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float4 A = __ldg(ba + k * f.stride), B = __ldg(bb + k * f.stride);
+            v[2 * k] = cp{make_float2(A.x, B.x), make_float2(A.y, B.y)};
+            v[2 * k + 1] = cp{make_float2(A.z, B.z), make_float2(A.w, B.w)};
+        }
+        return make_float2(1.f, 1.f);
+    } else {
+        const float2 sc =
+            make_float2(__ldg(f.scale + (long)ja * f.stride + y), __ldg(f.scale + (long)jb * f.stride + y));
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const uint4 A = __ldg(ba + k * f.stride), B = __ldg(bb + k * f.stride);
+            const __half2 *ha = reinterpret_cast<const __half2 *>(&A);
+            const __half2 *hb = reinterpret_cast<const __half2 *>(&B);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[4 * k + q] = cp{__half22float2(__lows2half2(ha[q], hb[q])), __half22float2(__highs2half2(ha[q], hb[q]))};
+        }
+        return sc;
+    }
+}
+
+// h = up - S (i s_mu dn) (t: up - S dn), components c of spins 0/1
+template <int MU, int S>
+__device__ __forceinline__ void project_p(const cp v[12], cp h[2][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cp u0 = v[c], u1 = v[3 + c], d0 = v[6 + c], d1 = v[9 + c];
+        if (MU == 0) {  // ta = i d1, tb = i d0
+            h[0][c] = cp{p_addsg<S>(u0.r, d1.i), p_addsg<-S>(u0.i, d1.r)};
+            h[1][c] = cp{p_addsg<S>(u1.r, d0.i), p_addsg<-S>(u1.i, d0.r)};
+        } else if (MU == 1) {  // ta = d1, tb = -d0
+            h[0][c] = cp{p_addsg<-S>(u0.r, d1.r), p_addsg<-S>(u0.i, d1.i)};
+            h[1][c] = cp{p_addsg<S>(u1.r, d0.r), p_addsg<S>(u1.i, d0.i)};
+        } else if (MU == 2) {  // ta = i d0, tb = -i d1
+            h[0][c] = cp{p_addsg<S>(u0.r, d0.i), p_addsg<-S>(u0.i, d0.r)};
+            h[1][c] = cp{p_addsg<-S>(u1.r, d1.i), p_addsg<S>(u1.i, d1.r)};
+        } else {  // ta = d0, tb = d1
+            h[0][c] = cp{p_addsg<-S>(u0.r, d0.r), p_addsg<-S>(u0.i, d0.i)};
+            h[1][c] = cp{p_addsg<-S>(u1.r, d1.r), p_addsg<-S>(u1.i, d1.i)};
+        }
+    }
+}
+
+// acc += (1 + S g_mu) psi from g = projected, multiplied two-spinor
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_p(cp acc[12], const cp g[2][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = cp{p_add(acc[c].r, g[0][c].r), p_add(acc[c].i, g[0][c].i)};
+        acc[3 + c] = cp{p_add(acc[3 + c].r, g[1][c].r), p_add(acc[3 + c].i, g[1][c].i)};
+        cp &l0 = acc[6 + c], &l1 = acc[9 + c];
+        if (MU == 0) {  // lower += S (i g1, i g0)
+            l0 = cp{p_addsg<-S>(l0.r, g[1][c].i), p_addsg<S>(l0.i, g[1][c].r)};
+            l1 = cp{p_addsg<-S>(l1.r, g[0][c].i), p_addsg<S>(l1.i, g[0][c].r)};
+        } else if (MU == 1) {  // lower += S (g1, -g0)
+            l0 = cp{p_addsg<S>(l0.r, g[1][c].r), p_addsg<S>(l0.i, g[1][c].i)};
+            l1 = cp{p_addsg<-S>(l1.r, g[0][c].r), p_addsg<-S>(l1.i, g[0][c].i)};
+        } else if (MU == 2) {  // lower += S (i g0, -i g1)
+            l0 = cp{p_addsg<-S>(l0.r, g[0][c].i), p_addsg<S>(l0.i, g[0][c].r)};
+            l1 = cp{p_addsg<S>(l1.r, g[1][c].i), p_addsg<-S>(l1.i, g[1][c].r)};
+        } else {  // lower -= S (g0, g1)
+            l0 = cp{p_addsg<-S>(l0.r, g[0][c].r), p_addsg<-S>(l0.i, g[0][c].i)};
+            l1 = cp{p_addsg<-S>(l1.r, g[1][c].r), p_addsg<-S>(l1.i, g[1][c].i)};
+        }
+    }
+}
+
+// g = U (sc h) or U^dag (sc h) for both lanes
+template <bool DAGU>
+__device__ __forceinline__ void link_mul_p(const float u[18], float2 sc, const cp h[2][3], cp g[2][3])
+{
+    cp hs[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hs[s][c] = cp{p_mul(h[s][c].r, sc), p_mul(h[s][c].i, sc)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cp acc0{bc(0.f), bc(0.f)}, acc1{bc(0.f), bc(0.f)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int k = DAGU ? 2 * (3 * b + a) : 2 * (3 * a + b);
+            const float2 ur = bc(u[k]), ui = bc(u[k + 1]), nui = bc(-u[k + 1]);
+            // U h:      re += ur hr - ui hi, im += ur hi + ui hr
+            // U^dag h:  re += ur hr + ui hi, im += ur hi - ui hr
+            const float2 x1 = DAGU ? ui : nui, x2 = DAGU ? nui : ui;
+            acc0.r = p_fma(ur, hs[0][b].r, acc0.r);
+            acc0.r = p_fma(x1, hs[0][b].i, acc0.r);
+            acc0.i = p_fma(ur, hs[0][b].i, acc0.i);
+            acc0.i = p_fma(x2, hs[0][b].r, acc0.i);
+            acc1.r = p_fma(ur, hs[1][b].r, acc1.r);
+            acc1.r = p_fma(x1, hs[1][b].i, acc1.r);
+            acc1.i = p_fma(ur, hs[1][b].i, acc1.i);
+            acc1.i = p_fma(x2, hs[1][b].r, acc1.i);
+        }
+        g[0][a] = acc0;
+        g[1][a] = acc1;
+    }
+}
+
+template <class S, int MU, int DIR, int SG>
+__device__ __forceinline__ void dir_p(const FastHop<S> &a, int ja, int jb, int i, int y, bool wrap, cp acc[12])
+{
+    constexpr int SP = DIR > 0 ? -SG : SG;
+    float u[18];
+    load_link18<S, float>(a.U, DIR > 0 ? a.parity : (a.parity ^ 1), MU, DIR > 0 ? i : y, u);
+    cp v[12];
+    const float2 sc = load_pair<S>(a.in, ja, jb, y, v);
+    cp h[2][3], g[2][3];
+    project_p<MU, SP>(v, h);
+    link_mul_p<(DIR < 0)>(u, sc, h, g);
+    if (wrap && ((a.theta_mask >> MU) & 1)) {
+        const float2 pr = bc(float(a.th_re[MU])), pi = bc(DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]));
+        const float2 npi = bc(DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]));
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const cp x = g[s][c];
+                g[s][c] = cp{p_fma(npi, x.i, p_mul(pr, x.r)), p_fma(pi, x.r, p_mul(pr, x.i))};
+            }
+    }
+    accumulate_p<MU, SP>(acc, g);
+}
+
+// out = A v for one Hermitian 6x6 block (36 floats), both lanes
+__device__ __forceinline__ void clov6_p(const float A[36], const cp *v, cp *o)
+{
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const float2 d = bc(A[r]);
+        cp acc{p_mul(d, v[r].r), p_mul(d, v[r].i)};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (c == r) continue;
+            const int lo = c > r ? r : c, hi = c > r ? c : r;
+            const int k = 6 + 2 * (lo * 5 - (lo * (lo - 1)) / 2 + (hi - lo - 1));
+            const float2 ur = bc(A[k]);
+            // entry (r, c) = A_k for c > r, conj(A_k) for c < r
+            const float2 ui = bc(c > r ? A[k + 1] : -A[k + 1]), nui = bc(c > r ? -A[k + 1] : A[k + 1]);
+            acc.r = p_fma(ur, v[c].r, acc.r);
+            acc.r = p_fma(nui, v[c].i, acc.r);
+            acc.i = p_fma(ur, v[c].i, acc.i);
+            acc.i = p_fma(ui, v[c].r, acc.i);
+        }
+        o[r] = acc;
+    }
+}
+
+template <class S, int MODE, bool DAG, bool NORM>
+__device__ __forceinline__ void hopp_group(const FastHop<S> &a, int tile, int g)
+{
+    const int ja0 = 2 * g, jb0 = 2 * g + 1;
+    const bool on_a = ja0 < a.nrhs && (!a.gate_st || a.gate_st[ja0].status == a.gate);
+    const bool on_b = jb0 < a.nrhs && (!a.gate_st || a.gate_st[jb0].status == a.gate);
+    if (!on_a && !on_b) return;
+    const int ja = min(ja0, a.nrhs - 1), jb = min(jb0, a.nrhs - 1);
+    const int i = tile * blockDim.x + threadIdx.x;
+    const bool valid = i < a.vh;
+    cp acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = cp{bc(0.f), bc(0.f)};
+    if (valid) {
+        const unsigned row = fdiv(unsigned(i), a.dx);
+        const int xh = i - int(row) * a.Lxh;
+        const unsigned q1 = fdiv(row, a.dy);
+        const int y = int(row) - int(q1) * a.L[1];
+        const unsigned q2 = fdiv(q1, a.dz);
+        const int z = int(q1) - int(q2) * a.L[2];
+        const int t = int(q2);
+        const int x = 2 * xh + ((a.parity + y + z + t) & 1);
+        const int rowbase = int(row) * a.Lxh;
+        constexpr int SG = DAG ? -1 : 1;
+        bool w;
+        w = x == a.L[0] - 1;
+        dir_p<S, 0, +1, SG>(a, ja, jb, i, rowbase + ((w ? 0 : x + 1) >> 1), w, acc);
+        w = x == 0;
+        dir_p<S, 0, -1, SG>(a, ja, jb, i, rowbase + ((w ? a.L[0] - 1 : x - 1) >> 1), w, acc);
+        w = y == a.L[1] - 1;
+        dir_p<S, 1, +1, SG>(a, ja, jb, i, i + (w ? -(a.L[1] - 1) * a.oy : a.oy), w, acc);
+        w = y == 0;
+        dir_p<S, 1, -1, SG>(a, ja, jb, i, i - (w ? -(a.L[1] - 1) * a.oy : a.oy), w, acc);
+        w = z == a.L[2] - 1;
+        dir_p<S, 2, +1, SG>(a, ja, jb, i, i + (w ? -(a.L[2] - 1) * a.oz : a.oz), w, acc);
+        w = z == 0;
+        dir_p<S, 2, -1, SG>(a, ja, jb, i, i - (w ? -(a.L[2] - 1) * a.oz : a.oz), w, acc);
+        w = t == a.L[3] - 1;
+        dir_p<S, 3, +1, SG>(a, ja, jb, i, i + (w ? -(a.L[3] - 1) * a.ot : a.ot), w, acc);
+        w = t == 0;
+        dir_p<S, 3, -1, SG>(a, ja, jb, i, i - (w ? -(a.L[3] - 1) * a.ot : a.ot), w, acc);
+    }
+    double n2a = 0.0, n2b = 0.0;
+    if (valid) {
+        cp res[12];
+        const float2 cf = bc(float(a.coef));
+        if constexpr (MODE == HOP_CLOV) {
+            float A[36];
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
+                clov6_p(A, acc + 6 * blk, res + 6 * blk);
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) res[q] = cp{p_mul(cf, res[q].r), p_mul(cf, res[q].i)};
+        } else {
+            cp sv[12];
+            const float2 sc = load_pair<S>(a.self, ja, jb, i, sv);
+            if constexpr (S::W == 8) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) sv[q] = cp{p_mul(sv[q].r, sc), p_mul(sv[q].i, sc)};
+            }
+            float A[36];
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
+                clov6_p(A, sv + 6 * blk, res + 6 * blk);
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) res[q] = cp{p_fma(cf, acc[q].r, res[q].r), p_fma(cf, acc[q].i, res[q].i)};
+        }
+        float va[24], vb[24];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            va[2 * q] = res[q].r.x;
+            va[2 * q + 1] = res[q].i.x;
+            vb[2 * q] = res[q].r.y;
+            vb[2 * q + 1] = res[q].i.y;
+        }
+        if (on_a) n2a = store_raw<S, float>(a.out, ja, i, va);
+        if (on_b) n2b = store_raw<S, float>(a.out, jb, i, vb);
+    }
+    if (NORM) {
+        if (on_a) reduce_finish(a.red, ja, tile, a.ntiles, n2a);
+        if (on_b) reduce_finish(a.red, jb, tile, a.ntiles, n2b);
+    }
+}
+
+// Block b handles tile b / nbt and pair groups [(b % nbt) gpb, ... + gpb).
+template <class S, int MODE, bool DAG, bool NORM, int MINB>
+__global__ void __launch_bounds__(128, MINB) hopp_kernel(const FastHop<S> a)
+{
+    const int ngr = (a.nrhs + 1) / 2;
+    const int nbt = (ngr + a.gpb - 1) / a.gpb;
+    int tile, gb;
+    if (!block_tile(a.ntiles, nbt, a.swz, tile, gb)) return;
+    const int g0 = gb * a.gpb;
+    const int g1 = min(ngr, g0 + a.gpb);
+    for (int g = g0; g < g1; ++g) hopp_group<S, MODE, DAG, NORM>(a, tile, g);
+}
+
+// ---------------------------------------------------------------------------
+// Prefetching variant (one right-hand side per thread, FP16 / FP32 storage):
+// the raw words of the links and neighbour spinors of PF directions are
+// loaded before any of them is used, so a thread has PF directions of loads
+// in flight instead of one (the kernel is bound by load latency otherwise).
+// ---------------------------------------------------------------------------
+template <class S>
+struct RawSpinor {
+    typename S::word w[spinor_planes<S>::n];
+    float sc;
+};
+template <class S>
+struct RawLink {
+    typename S::word w[S::W == 4 ? 3 : 1];
+    uint2 w2;  // FP16 only
+};
+
+template <class S>
+__device__ __forceinline__ void fetch_spinor(const SpinorField<S> &f, int j, int y, RawSpinor<S> &r)
+{
+    constexpr int NP = spinor_planes<S>::n;
+    const typename S::word *b = f.p + (long)j * NP * f.stride + y;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) r.w[k] = __ldg(b + k * f.stride);
+    if constexpr (S::W == 8) r.sc = __ldg(f.scale + (long)j * f.stride + y);
+    else r.sc = 1.f;
+}
+
+template <class S>
+__device__ __forceinline__ void fetch_link(const LinkField<S> &f, int parity, int mu, int i, RawLink<S> &r)
+{
+    if constexpr (S::W == 4) {
+        const float4 *b = f.p + (long)(parity * 4 + mu) * 3 * f.stride + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r.w[k] = __ldg(b + k * f.stride);
+    } else {
+        r.w[0] = __ldg(f.p + (long)(parity * 4 + mu) * f.stride + i);
+        r.w2 = __ldg(f.p2 + (long)(parity * 4 + mu) * f.stride + i);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void decode_spinor(const RawSpinor<S> &r, float v[24])
+{
+    constexpr int NP = spinor_planes<S>::n;
+    if constexpr (S::W == 4) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            v[4 * k] = r.w[k].x;
+            v[4 * k + 1] = r.w[k].y;
+            v[4 * k + 2] = r.w[k].z;
+            v[4 * k + 3] = r.w[k].w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const __half2 *h = reinterpret_cast<const __half2 *>(&r.w[k]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 t = __half22float2(h[q]);
+                v[8 * k + 2 * q] = t.x;
+                v[8 * k + 2 * q + 1] = t.y;
+            }
+        }
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void decode_link(const RawLink<S> &r, float u[18])
+{
+    if constexpr (S::W == 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            u[4 * k] = r.w[k].x;
+            u[4 * k + 1] = r.w[k].y;
+            u[4 * k + 2] = r.w[k].z;
+            u[4 * k + 3] = r.w[k].w;
+        }
+    } else {
+        const __half2 *h = reinterpret_cast<const __half2 *>(&r.w[0]);
+        const __half2 *h2 = reinterpret_cast<const __half2 *>(&r.w2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float2 t = __half22float2(h[e]);
+            u[2 * e] = t.x;
+            u[2 * e + 1] = t.y;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float2 t = __half22float2(h2[e]);
+            u[8 + 2 * e] = t.x;
+            u[9 + 2 * e] = t.y;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a = (c + 1) % 3, b = (c + 2) % 3;
+        float re = 0.f, im = 0.f;
+        cmad(re, im, u[2 * a], u[2 * a + 1], u[6 + 2 * b], u[7 + 2 * b]);
+        cmad(re, im, -u[2 * b], -u[2 * b + 1], u[6 + 2 * a], u[7 + 2 * a]);
+        u[12 + 2 * c] = re;
+        u[13 + 2 * c] = -im;
+    }
+}
+
+// direction d = 2 mu + (0 forward, 1 backward)
+template <class S, int D, int SG>
+__device__ __forceinline__ void compute_dir(const FastHop<S> &a, const RawLink<S> &rl, const RawSpinor<S> &rs,
+                                            bool wrap, float acc[24])
+{
+    constexpr int MU = D / 2, DIR = (D & 1) ? -1 : 1;
+    constexpr int SP = DIR > 0 ? -SG : SG;
+    float u[18], v[24];
+    decode_link<S>(rl, u);
+    decode_spinor<S>(rs, v);
+    float hr[2][3], hi[2][3], gr[2][3], gi[2][3];
+    project_f<MU, SP, float>(v, hr, hi);
+    link_mul<(DIR < 0), float>(u, rs.sc, hr, hi, gr, gi);
+    if (wrap && ((a.theta_mask >> MU) & 1)) {
+        const float pr = float(a.th_re[MU]), pi = DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float xr = gr[s][c], xi = gi[s][c];
+                gr[s][c] = pr * xr - pi * xi;
+                gi[s][c] = pr * xi + pi * xr;
+            }
+    }
+    accumulate_f<MU, SP, float>(acc, gr, gi);
+}
+
+template <class S, int D0, int PF, int SG>
+__device__ __forceinline__ void phase_dirs(const FastHop<S> &a, int j, int i, const int (&nb)[8], unsigned wrapm,
+                                           float acc[24])
+{
+    RawLink<S> rl[PF];
+    RawSpinor<S> rs[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+        const int d = D0 + q;
+        fetch_link<S>(a.U, (d & 1) ? (a.parity ^ 1) : a.parity, d / 2, (d & 1) ? nb[d] : i, rl[q]);
+        fetch_spinor<S>(a.in, j, nb[d], rs[q]);
+    }
+    if constexpr (PF == 8) {
+        compute_dir<S, D0 + 0, SG>(a, rl[0], rs[0], (wrapm >> (D0 + 0)) & 1, acc);
+        compute_dir<S, D0 + 1, SG>(a, rl[1], rs[1], (wrapm >> (D0 + 1)) & 1, acc);
+        compute_dir<S, D0 + 2, SG>(a, rl[2], rs[2], (wrapm >> (D0 + 2)) & 1, acc);
+        compute_dir<S, D0 + 3, SG>(a, rl[3], rs[3], (wrapm >> (D0 + 3)) & 1, acc);
+        compute_dir<S, D0 + 4, SG>(a, rl[4], rs[4], (wrapm >> (D0 + 4)) & 1, acc);
+        compute_dir<S, D0 + 5, SG>(a, rl[5], rs[5], (wrapm >> (D0 + 5)) & 1, acc);
+        compute_dir<S, D0 + 6, SG>(a, rl[6], rs[6], (wrapm >> (D0 + 6)) & 1, acc);
+        compute_dir<S, D0 + 7, SG>(a, rl[7], rs[7], (wrapm >> (D0 + 7)) & 1, acc);
+    } else if constexpr (PF == 4) {
+        compute_dir<S, D0 + 0, SG>(a, rl[0], rs[0], (wrapm >> (D0 + 0)) & 1, acc);
+        compute_dir<S, D0 + 1, SG>(a, rl[1], rs[1], (wrapm >> (D0 + 1)) & 1, acc);
+        compute_dir<S, D0 + 2, SG>(a, rl[2], rs[2], (wrapm >> (D0 + 2)) & 1, acc);
+        compute_dir<S, D0 + 3, SG>(a, rl[3], rs[3], (wrapm >> (D0 + 3)) & 1, acc);
+    } else {
+        compute_dir<S, D0 + 0, SG>(a, rl[0], rs[0], (wrapm >> (D0 + 0)) & 1, acc);
+        compute_dir<S, D0 + 1, SG>(a, rl[1], rs[1], (wrapm >> (D0 + 1)) & 1, acc);
+    }
+}
+
+template <class S, int MODE, bool DAG, bool NORM, int PF>
+__device__ __forceinline__ void hopq_item(const FastHop<S> &a, int tile, int j)
+{
+    if (a.gate_st && a.gate_st[j].status != a.gate) return;
+    const int i = tile * blockDim.x + threadIdx.x;
+    const bool valid = i < a.vh;
+    double n2 = 0.0;
+    if (valid) {
+        const unsigned row = fdiv(unsigned(i), a.dx);
+        const int xh = i - int(row) * a.Lxh;
+        const unsigned q1 = fdiv(row, a.dy);
+        const int y = int(row) - int(q1) * a.L[1];
+        const unsigned q2 = fdiv(q1, a.dz);
+        const int z = int(q1) - int(q2) * a.L[2];
+        const int t = int(q2);
+        const int x = 2 * xh + ((a.parity + y + z + t) & 1);
+        const int rowbase = int(row) * a.Lxh;
+        int nb[8];
+        unsigned wm = 0;
+        bool w;
+        w = x == a.L[0] - 1; wm |= unsigned(w) << 0; nb[0] = rowbase + ((w ? 0 : x + 1) >> 1);
+        w = x == 0;          wm |= unsigned(w) << 1; nb[1] = rowbase + ((w ? a.L[0] - 1 : x - 1) >> 1);
+        w = y == a.L[1] - 1; wm |= unsigned(w) << 2; nb[2] = i + (w ? -(a.L[1] - 1) * a.oy : a.oy);
+        w = y == 0;          wm |= unsigned(w) << 3; nb[3] = i - (w ? -(a.L[1] - 1) * a.oy : a.oy);
+        w = z == a.L[2] - 1; wm |= unsigned(w) << 4; nb[4] = i + (w ? -(a.L[2] - 1) * a.oz : a.oz);
+        w = z == 0;          wm |= unsigned(w) << 5; nb[5] = i - (w ? -(a.L[2] - 1) * a.oz : a.oz);
+        w = t == a.L[3] - 1; wm |= unsigned(w) << 6; nb[6] = i + (w ? -(a.L[3] - 1) * a.ot : a.ot);
+        w = t == 0;          wm |= unsigned(w) << 7; nb[7] = i - (w ? -(a.L[3] - 1) * a.ot : a.ot);
+        constexpr int SG = DAG ? -1 : 1;
+        float acc[24];
+#pragma unroll
+        for (int q = 0; q < 24; ++q) acc[q] = 0.f;
+        if constexpr (PF == 8) {
+            phase_dirs<S, 0, 8, SG>(a, j, i, nb, wm, acc);
+        } else if constexpr (PF == 4) {
+            phase_dirs<S, 0, 4, SG>(a, j, i, nb, wm, acc);
+            phase_dirs<S, 4, 4, SG>(a, j, i, nb, wm, acc);
+        } else {
+            phase_dirs<S, 0, 2, SG>(a, j, i, nb, wm, acc);
+            phase_dirs<S, 2, 2, SG>(a, j, i, nb, wm, acc);
+            phase_dirs<S, 4, 2, SG>(a, j, i, nb, wm, acc);
+            phase_dirs<S, 6, 2, SG>(a, j, i, nb, wm, acc);
+        }
+        float res[24];
+        const float coef = float(a.coef);
+        if constexpr (MODE == HOP_CLOV) {
+            float A[36];
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
+                clov6(A, acc + 12 * blk, res + 12 * blk);
+            }
+#pragma unroll
+            for (int q = 0; q < 24; ++q) res[q] *= coef;
+        } else {
+            float sv[24];
+            const float sc = load_raw<S, float>(a.self, j, i, sv);
+            if constexpr (S::W == 8) {
+#pragma unroll
+                for (int q = 0; q < 24; ++q) sv[q] *= sc;
+            }
+            float A[36];
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
+                clov6(A, sv + 12 * blk, res + 12 * blk);
+            }
+#pragma unroll
+            for (int q = 0; q < 24; ++q) res[q] = fmaf(coef, acc[q], res[q]);
+        }
+        n2 = store_raw<S, float>(a.out, j, i, res);
+    }
+    if (NORM) reduce_finish(a.red, j, tile, a.ntiles, n2);
+}
+
+// Block b handles tile b / nbt and right-hand sides [(b % nbt) gpb, ... + gpb).
+template <class S, int MODE, bool DAG, bool NORM, int PF>
+__global__ void __launch_bounds__(128) hopq_kernel(const FastHop<S> a)
+{
+    const int nbt = (a.nrhs + a.gpb - 1) / a.gpb;
+    int tile, gb;
+    if (!block_tile(a.ntiles, nbt, a.swz, tile, gb)) return;
+    const int j0 = gb * a.gpb;
+    const int j1 = min(a.nrhs, j0 + a.gpb);
+    for (int j = j0; j < j1; ++j) hopq_item<S, MODE, DAG, NORM, PF>(a, tile, j);
 }
 
 }  // namespace lqcd

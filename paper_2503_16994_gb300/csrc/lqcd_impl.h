@@ -160,7 +160,7 @@ struct ProfScope {
 };
 
 // records an autotuning decision (reported by lqcd_tune_report)
-void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, float ms);
+void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, int minb, int swz, float ms);
 
 // algorithmic bytes per site of one field in a storage format
 template <class S> constexpr double spinor_bytes() { return S::W == 2 ? 192.0 : (S::W == 4 ? 96.0 : 52.0); }

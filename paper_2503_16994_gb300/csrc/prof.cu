@@ -86,14 +86,15 @@ std::mutex g_tune_mu;
 std::string g_tune;  // JSON objects, comma separated
 }  // namespace
 
-void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, float ms)
+void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, int minb, int swz, float ms)
 {
     static const char *modes[] = {"hopclov", "selfclov", "self", "clovsum", "resid"};
-    char buf[320];
+    char buf[400];
     std::snprintf(buf, sizeof buf,
                   "{\"kernel\": \"hop_%s_%s\", \"sites\": %d, \"nrhs\": %d, \"rhs_per_thread\": %d, "
-                  "\"rhs_groups_per_block\": %d, \"block\": %d, \"us\": %.2f}",
-                  prec, modes[mode], vh, nrhs, nr, gpb, kBlock, ms * 1e3);
+                  "\"rhs_groups_per_block\": %d, \"min_blocks_per_sm\": %d, \"tiles_per_supertile\": %d, "
+                  "\"block\": %d, \"us\": %.2f}",
+                  prec, modes[mode], vh, nrhs, nr, gpb, minb, swz, kBlock, ms * 1e3);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (!g_tune.empty()) g_tune += ", ";
     g_tune += buf;

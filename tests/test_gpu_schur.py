@@ -89,3 +89,41 @@ def test_schur_low_precision_against_fp64(lq, dims, prec, tol):
             assert np.array_equal(one, got[1])
     finally:
         lq.lattice_destroy(lat)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 4e-3)])
+def test_every_kernel_shape_agrees(lq, prec, tol, monkeypatch):
+    """Forces each hopping-kernel shape the autotuner can pick (two right-hand
+    sides per thread in packed FP32x2 lanes, 1-3 per thread in scalar
+    arithmetic, or one per thread with 2/4/8 directions of loads issued
+    ahead, times groups per block and the super-tile block order) and checks
+    it against FP64."""
+    import torch
+    dims, kappa, csw = (6, 4, 4, 10), 0.13, 1.6
+    U = inputs.gauge_field(dims, 0.4, seed=21)
+    ev = parity_mask(dims)
+    nrhs = 5  # odd: exercises a half-empty last pair / group
+    x = inputs.spinor_field(dims, seed=22, nrhs=nrhs) * ev
+    lat = lq.lattice_create(dims)
+    try:
+        gid = lq.gauge_upload(lat, U)
+        dp = lq.dirac_params(kappa, csw, (1, np.exp(0.3j), 1, -1))
+        xt = torch.from_numpy(x).cuda()
+        outs = {}
+        for dag in (False, True):
+            ref = lq.schur_apply(lat, gid, dp, xt, precision="fp64", nrhs=nrhs, dagger=dag).cpu().numpy()
+            for nr, gpb, swz in [(0, 1, 1), (0, 3, 1), (0, 1, 8), (1, 1, 1), (1, 5, 1), (1, 1, 8), (2, 1, 1), (2, 3, 1),
+                                 (3, 1, 32), (-2, 1, 1), (-4, 5, 1), (-8, 1, 8)]:
+                monkeypatch.setenv("LQCD_HOP_NR", str(nr))
+                monkeypatch.setenv("LQCD_HOP_GPB", str(gpb))
+                monkeypatch.setenv("LQCD_HOP_SWZ", str(swz))
+                got = lq.schur_apply(lat, gid, dp, xt, precision=prec, nrhs=nrhs, dagger=dag).cpu().numpy()
+                for j in range(nrhs):
+                    assert rel(got[j], ref[j]) <= tol, (nr, gpb, j)
+                outs[(dag, nr, gpb, swz)] = got
+            base = outs[(dag, 1, 1, 1)]
+            for k, v in outs.items():
+                if k[0] == dag:
+                    assert rel(v, base) <= 50 * (2e-7 if prec == "fp32" else 1e-3), k
+    finally:
+        lq.lattice_destroy(lat)
