@@ -147,6 +147,15 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
         auto it = table.find(key);
         if (it != table.end()) return it->second;
     }
+    // one tuning at a time in the process (server slots may ask concurrently);
+    // whoever waited finds the result in the table
+    static std::mutex tuning;
+    std::lock_guard<std::mutex> tl(tuning);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = table.find(key);
+        if (it != table.end()) return it->second;
+    }
     std::vector<HopShape> cand;
     const int maxnr = std::is_same<S, F64>::value ? 1 : 3;
     for (int nr = (std::is_same<S, F64>::value || f.nrhs < 2) ? 1 : 0; nr <= maxnr && nr <= f.nrhs; ++nr) {
@@ -154,6 +163,11 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
         const int ngr = (f.nrhs + per - 1) / per;
         for (int gpb : {1, 2, 3, 4, 6, 12})
             if (gpb <= ngr && (gpb == 1 || ngr % gpb == 0)) {
+                // FP64 is bound by the FP64 units: only the grouping is worth timing
+                if (std::is_same<S, F64>::value) {
+                    if (gpb <= 2) cand.push_back(HopShape{nr, gpb, 1, 1});
+                    continue;
+                }
                 for (int swz : {1, 8, 32}) {
                     if (swz > 1 && ngr / gpb < 2) continue;  // one block per tile: order is irrelevant
                     cand.push_back(HopShape{nr, gpb, 1, swz});
@@ -177,7 +191,7 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
         f.swz = c.swz;
         hopf_launch<S>(f, c.nr, mode, false, false, st);  // warm-up
         float ms_min = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 2; ++rep) {
             LQCD_CUDA(cudaEventRecord(e0, st));
             hopf_launch<S>(f, c.nr, mode, false, false, st);
             LQCD_CUDA(cudaEventRecord(e1, st));
