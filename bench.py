@@ -319,6 +319,61 @@ def serving_measure(lqcd, n_requests, rate=None):
 
 
 # ---------------------------------------------------------------------------
+# batched uneven propagators (lqcd_pion_corr_batch)
+# ---------------------------------------------------------------------------
+BATCH = {"sizes": [[8, 8, 8, 16], [12, 12, 12, 24], [16, 16, 16, 32], [24, 24, 24, 48]], "per_size": 16,
+         "eps": 0.3, "csw": 1.5, "kappa": [0.120, 0.132], "precision": "fp16", "tol": 1e-10, "seed": 11}
+
+
+def batch_measure(lqcd, per_size=None):
+    """64 propagators (16 per size) in one lqcd_pion_corr_batch call, against
+    the same jobs solved one after another (lqcd_pion_corr, same precision)
+    and an FP64 sequential estimate (one FP64 propagator per size, x per_size)."""
+    import torch
+    from paper_2503_16994_gb300 import inputs
+    per = per_size or BATCH["per_size"]
+    lats, jobs, T = [], [], []
+    kap = inputs.kappa_values(BATCH["seed"], per * len(BATCH["sizes"]), *BATCH["kappa"])
+    try:
+        k = 0
+        for si, dims in enumerate(BATCH["sizes"]):
+            U = inputs.gauge_field(dims, BATCH["eps"], seed=BATCH["seed"] + 1 + si, workers=None)
+            lat = lqcd.lattice_create(dims)
+            lats.append(lat)
+            g = lqcd.gauge_upload(lat, U)
+            for _ in range(per):
+                jobs.append((lat, g, lqcd.dirac_params(float(kap[k]), BATCH["csw"]), (0, 0, 0, 0), dims[3]))
+                k += 1
+        sp = lqcd.solver_params(tol=BATCH["tol"], maxiter=20000, precision=BATCH["precision"])
+        lqcd.pion_corr_batch(jobs[:len(BATCH["sizes"])], sp)  # warm-up: clover fields, workspaces, tuning
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, infos, st, rc = lqcd.pion_corr_batch(jobs, sp)
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for lat, g, dp, src, Tn in jobs:
+            lqcd.pion_corr(lat, g, dp, sp, src, dims=(1, 1, 1, Tn))
+        tseq = time.perf_counter() - t0
+        sp64 = lqcd.solver_params(tol=BATCH["tol"], maxiter=20000, precision="fp64")
+        t64 = 0.0
+        for si in range(len(BATCH["sizes"])):
+            lat, g, dp, src, Tn = jobs[si * per]
+            t0 = time.perf_counter()
+            lqcd.pion_corr(lat, g, dp, sp64, src, dims=(1, 1, 1, Tn))
+            t64 += (time.perf_counter() - t0) * per
+    finally:
+        for lat in lats:
+            lqcd.lattice_destroy(lat)
+    n = 12 * len(jobs)
+    return {"propagators": len(jobs), "converged": rc == lqcd.OK, "batched_solves_per_s": n / tb,
+            "sequential_mixed_solves_per_s": n / tseq, "sequential_fp64_solves_per_s_est": n / t64,
+            "batched_vs_sequential_mixed": tseq / tb, "batched_vs_sequential_fp64_est": t64 / tb,
+            "batched_s": tb, "tuning": [t for t in lqcd.tune_report() if t["nrhs"] == 12],
+            "workload": "16 each of 8^3x16, 12^3x24, 16^3x32, 24^3x48; eps 0.3; kappa U[0.120,0.132]; csw 1.5; "
+                        "12 RHS FP16 mixed; tol 1e-10; one graph per chunk of 8 iterations"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -442,6 +497,7 @@ def run_ours(args):
 
     dslash = None if args.no_dslash else dslash_measure(lqcd, lat, gid, dp, dims)
     serving = None if (args.serve_requests <= 0 or rank != 0) else serving_measure(lqcd, args.serve_requests)
+    batch = None if (args.no_batch or rank != 0) else batch_measure(lqcd)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -460,7 +516,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": None, "kernel": "hop_f16_* (hopclov + selfclov)",
                          "peak_source": f"{peak_kind} hbm_gbs", "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS,
                          "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None},
-            "dslash": dslash, "serving": serving, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "dslash": dslash, "serving": serving, "batched": batch, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
             "fp64_gpu": fp64, "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
             "iters": {"inner_max": max(i["iters_inner"] for i in infos_last),
                       "outer_max": max(i["iters_outer"] for i in infos_last),
@@ -517,6 +573,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
     ap.add_argument("--dslash-only", action="store_true", help="time only the Dslash on --lattice")
     ap.add_argument("--lattice", default="32,32,32,64")

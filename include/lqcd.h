@@ -202,6 +202,33 @@ int lqcd_pion_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
                    const lqcd_solver_params *sp, const int src[4], double *corr, double *prop,
                    lqcd_solve_info *info, int flags, void *stream);
 
+/* One job of a batch of point-source propagators: its lattice and resident
+ * gauge field, Dirac parameters, source, and outputs. */
+typedef struct {
+    lqcd_lattice lat;           /* in: lattice of this job (jobs may share one) */
+    int gauge_id;               /* in: resident gauge field on lat */
+    lqcd_dirac_params dp;       /* in: kappa, csw, theta of this job */
+    int src[4];                 /* in: source position {x, y, z, t} */
+    double *corr;               /* out: host array of T doubles (T of this lattice) */
+    lqcd_solve_info info[12];   /* out: per column */
+    int status;                 /* out: LQCD_OK or LQCD_ENOCONV */
+} lqcd_pion_job;
+
+/* Many point-source propagators (lqcd_pion_corr per job) on lattices of
+ * different sizes, gauge fields and kappa, solved together: every job's 12
+ * columns iterate in the same CUDA graph (one branch per job, `chunk`
+ * iterations per graph launch, 0 = 8), so the device runs all lattices at
+ * once and the host issues one launch per chunk instead of one per kernel.
+ * The benchmark spec's batched uneven solves; the paper solves one propagator at
+ * a time (Sec. 4 example).  All jobs use sp (precision, tol, maxiter) and
+ * the device of their lattices (one device for the batch).  The call locks
+ * every lattice involved and returns when all jobs are done; `stream` work
+ * queued before the call completes first.
+ * Returns LQCD_OK, LQCD_ENOCONV when a job has a column that did not
+ * converge (its status says which), or an error (LQCD_EINVAL, LQCD_ENOMEM,
+ * LQCD_ECUDA). */
+int lqcd_pion_corr_batch(lqcd_pion_job *jobs, int njobs, const lqcd_solver_params *sp, int chunk, void *stream);
+
 /* The pion contraction alone: corr[t] as above from 12 columns prop (12 * 24 V
  * doubles, host layout) with the source on time slice src_t.  Host pointers,
  * or device pointers with LQCD_DEVICE_PTRS.  Uses a device scratch buffer

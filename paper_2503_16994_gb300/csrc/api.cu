@@ -1,6 +1,7 @@
 // The C ABI (include/lqcd.h): argument checks, host/device buffer handling,
 // error reporting.  No call aborts: every failure becomes a status code with
 // a thread-local message.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -270,6 +271,45 @@ int lqcd_pion_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, 
         LQCD_CUDA(cudaStreamSynchronize(st));
     }
     if (failed) return fail(LQCD_ENOCONV, std::to_string(failed) + " column(s) did not converge");
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_pion_corr_batch(lqcd_pion_job *jobs, int njobs, const lqcd_solver_params *sp, int chunk, void *stream)
+{
+    if (!jobs || njobs < 1) return fail(LQCD_EINVAL, "no jobs");
+    if (int rc = check_solver(sp)) return rc;
+    if (chunk < 0 || chunk > 1024) return fail(LQCD_EINVAL, "chunk must be in 0..1024");
+    std::vector<lqcd_lattice_s *> lats;
+    for (int k = 0; k < njobs; ++k) {
+        const lqcd_pion_job &j = jobs[k];
+        if (!j.lat || !j.corr) return fail(LQCD_EINVAL, "null lattice or corr in job " + std::to_string(k));
+        if (int rc = check_params(&j.dp)) return rc;
+        for (int m = 0; m < 4; ++m)
+            if (j.src[m] < 0 || j.src[m] >= j.lat->dims[m])
+                return fail(LQCD_EINVAL, "source outside the lattice in job " + std::to_string(k));
+        if (j.lat->device != jobs[0].lat->device) return fail(LQCD_EINVAL, "all jobs must use the same device");
+        lats.push_back(j.lat);
+    }
+    std::sort(lats.begin(), lats.end());
+    lats.erase(std::unique(lats.begin(), lats.end()), lats.end());
+    API_TRY
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (lqcd_lattice_s *l : lats) locks.emplace_back(l->mu);  // address order: no lock-order inversion
+    DeviceGuard dg(jobs[0].lat->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t origin = nullptr;
+    LQCD_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+    int failed = 0;
+    try {
+        LQCD_CUDA(cudaStreamSynchronize(st));
+        failed = pion_batch(jobs, njobs, *sp, chunk ? chunk : 8, origin);
+    } catch (...) {
+        cudaStreamDestroy(origin);
+        throw;
+    }
+    cudaStreamDestroy(origin);
+    if (failed) return fail(LQCD_ENOCONV, std::to_string(failed) + " job(s) had a column that did not converge");
     return LQCD_OK;
     API_CATCH
 }

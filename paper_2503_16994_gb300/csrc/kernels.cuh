@@ -10,7 +10,9 @@ namespace lqcd {
 // ---------------------------------------------------------------------------
 // per right-hand-side solver state (device resident, one struct per RHS)
 // ---------------------------------------------------------------------------
-enum RhsStatus : int { ST_DONE = 0, ST_ACTIVE = 1, ST_UPDATE = 2, ST_MAXITER = 3, ST_IDLE = 4 };
+// ST_RESUME: just updated in FP64 while the others went on (batched
+// solves); runs the second half of its iteration, then becomes ST_ACTIVE.
+enum RhsStatus : int { ST_DONE = 0, ST_ACTIVE = 1, ST_UPDATE = 2, ST_MAXITER = 3, ST_IDLE = 4, ST_RESUME = 5 };
 
 struct RhsState {
     double gamma;    // |z|^2, z = Dhat^dag r (CGLS)
@@ -26,6 +28,7 @@ struct RhsState {
     int iter;
     int updates;
     int maxiter;
+    int resume;      // status after an FP64 residual that did not finish: ST_ACTIVE or ST_RESUME
 };
 
 // What the last block does with a finished per-RHS sum.
@@ -72,7 +75,7 @@ __device__ __forceinline__ void apply_op(const Reduce &r, int j, double sum)
         else if (s.iter >= s.maxiter || !(sum == sum))
             s.status = ST_MAXITER;
         else
-            s.status = ST_ACTIVE;
+            s.status = s.resume;
         break;
     }
 }

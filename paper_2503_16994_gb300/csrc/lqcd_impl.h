@@ -221,6 +221,10 @@ void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
 int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,
           const double *b_dev, double *x_dev, const int *src, int nrhs, lqcd_solve_info *info, double *corr_dev,
           cudaStream_t st);
+// Batched propagators over uneven lattices (lqcd_pion_corr_batch); returns
+// the number of jobs with a column that did not converge.
+int pion_batch(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int chunk, cudaStream_t origin);
+
 // The same on explicit clover fields and workspace (no lattice caches); stops
 // early when *cancel becomes true (then returns nrhs).
 int solve_on(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,

@@ -63,7 +63,8 @@ ProfScope::ProfScope(const char *name_, double bytes_, cudaStream_t st_) : name(
     Stat &s = g_stats[name];
     s.launches += 1;
     s.bytes += bytes;
-    if (g_timing) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (g_timing && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
         a = get_event();
         b = get_event();
         LQCD_CUDA(cudaEventRecord(a, st));

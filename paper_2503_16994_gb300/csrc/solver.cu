@@ -127,7 +127,7 @@ static Workspace &workspace(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_
     return ref;
 }
 
-__global__ void init_state_kernel(RhsState *s, int nrhs, double tol2, double delta2, int maxiter)
+__global__ void init_state_kernel(RhsState *s, int nrhs, double tol2, double delta2, int maxiter, int resume)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nrhs) return;
@@ -142,7 +142,20 @@ __global__ void init_state_kernel(RhsState *s, int nrhs, double tol2, double del
     q.rr = q.rr_ref = 0.0;
     q.iter = 0;
     q.updates = -1;  // the first FP64 residual (of the zero start) is not an update
+    q.resume = resume;
     s[j] = q;
+}
+
+__global__ void set_resume_kernel(RhsState *s, int nrhs, int v)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nrhs) s[j].resume = v;
+}
+
+__global__ void status_change_kernel(RhsState *s, int nrhs, int from, int to)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nrhs && s[j].status == from) s[j].status = to;
 }
 
 template <class W, class E>
@@ -221,6 +234,8 @@ struct Solver {
     }
 
     // |b|^2, bhat = b_e + k H_eo A_oo^-1 b_o, state initialisation, x = e = p = 0
+    int resume = ST_ACTIVE;  // ST_RESUME for batched solves (the update happens between graph chunks)
+
     void prepare(double tol_eff, double delta, int maxiter)
     {
         VecArgs q = v;
@@ -236,7 +251,8 @@ struct Solver {
         a.out = bhat;
         a.coef = kappa;
         launch_hop(a, SELF_PLAIN, false, false, st);
-        init_state_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(S, nrhs, tol_eff * tol_eff, delta * delta, maxiter);
+        init_state_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(S, nrhs, tol_eff * tol_eff, delta * delta, maxiter,
+                                                           resume);
         LQCD_CHECK_LAUNCH();
         LQCD_CUDA(cudaMemsetAsync(ws.x_e.p, 0, ws.x_e.bytes, st));
         LQCD_CUDA(cudaMemsetAsync(ws.e.p, 0, ws.e.bytes, st));
@@ -290,12 +306,12 @@ struct Solver {
         launch_er_update<W, E>(gated(ST_ACTIVE, RED_RUPDATE), p, w, r, e, st);
     }
 
-    // z = Dhat^dag r (|z|^2 -> beta, gamma); p = z + beta p   [gate ACTIVE]
-    void half2()
+    // z = Dhat^dag r (|z|^2 -> beta, gamma); p = z + beta p   [gate ACTIVE or RESUME]
+    void half2(int gate = ST_ACTIVE)
     {
         HopArgs<W, W, W> a = hw;
         a.gate_st = S;
-        a.gate = ST_ACTIVE;
+        a.gate = gate;
         a.parity = 1;
         a.in = r;
         a.out = t;
@@ -310,7 +326,21 @@ struct Solver {
         a.coef = -kappa;
         a.red.op = RED_BETA;
         launch_hop(a, SELF_CLOV, true, true, st);
-        launch_p_update<W>(gated(ST_ACTIVE, RED_STORE), S, z, p, st);
+        launch_p_update<W>(gated(gate, RED_STORE), S, z, p, st);
+    }
+
+    void set_resume(int v)
+    {
+        set_resume_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(S, nrhs, v);
+        LQCD_CHECK_LAUNCH();
+    }
+
+    // right-hand sides just updated in FP64 finish their iteration, then rejoin
+    void resumed_to_active()
+    {
+        half2(ST_RESUME);
+        status_change_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(S, nrhs, ST_RESUME, ST_ACTIVE);
+        LQCD_CHECK_LAUNCH();
     }
 
     // x_o = A_oo^-1 (b_o + k H_oe x_e); acc = |b - D x|^2 over both parities
@@ -388,44 +418,59 @@ struct Solver {
 
     const volatile bool *cancel = nullptr;  // set by the server: stop at the next poll
 
-    // returns the number of RHS that did not reach tol
-    int run(const lqcd_solver_params &sp, lqcd_solve_info *info)
+    double tol_ = 0, delta_ = 0;
+
+    // |b|, bhat, the FP64 residual of the zero start and the first z, p
+    void start(const lqcd_solver_params &sp)
     {
-        const double delta = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : 0.1);
-        const double tol = sp.tol;
-        prepare(0.5 * tol, delta, sp.maxiter);
+        delta_ = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : 0.1);
+        tol_ = sp.tol;
+        prepare(0.5 * tol_, delta_, sp.maxiter);
         reliable_update();
         half2();
-        // Large batches: read the states after every half-iteration and launch
-        // the FP64 update only when some RHS asked for it (a gated-off launch
-        // of the FP64 kernels still schedules every block; the host round trip
-        // costs ~15 us against milliseconds of work).  Small batches: gated
-        // launches are cheap, so poll every few iterations only.
+    }
+
+    // Iterates until every RHS is done or capped.  Large batches: read the
+    // states after every half-iteration and launch the FP64 update only when
+    // some RHS asked for it (a gated-off launch of the FP64 kernels still
+    // schedules every block; the host round trip costs ~15 us against
+    // milliseconds of work).  Small batches: gated launches are cheap, so
+    // poll every few iterations only.
+    void iterate(const lqcd_solver_params &sp)
+    {
         const bool poll_each = long(lat->vh) * nrhs >= (1L << 20);
         const int chunk = poll_each ? 1 : 8;
-        for (int attempt = 0; attempt < 4; ++attempt) {
-            long guard = (long)sp.maxiter + 64;
-            bool finished = false;
-            for (long it = 0; it < guard && !finished && !(cancel && *cancel); it += chunk) {
-                for (int k = 0; k < chunk; ++k) {
-                    half1();
-                    if (poll_each) {
-                        pull_states();
-                        if (all_finished()) {
-                            finished = true;
-                            break;
-                        }
-                        if (any_status(ST_UPDATE)) reliable_update();
-                    } else {
-                        reliable_update();
-                    }
-                    half2();
-                }
-                if (!poll_each) {
+        long guard = (long)sp.maxiter + 64;
+        bool finished = false;
+        for (long it = 0; it < guard && !finished && !(cancel && *cancel); it += chunk) {
+            for (int k = 0; k < chunk; ++k) {
+                half1();
+                if (poll_each) {
                     pull_states();
-                    finished = all_finished();
+                    if (all_finished()) {
+                        finished = true;
+                        break;
+                    }
+                    if (any_status(ST_UPDATE)) reliable_update();
+                } else {
+                    reliable_update();
                 }
+                half2();
             }
+            if (!poll_each) {
+                pull_states();
+                finished = all_finished();
+            }
+        }
+    }
+
+    // x_o, true residuals; RHS whose full-lattice residual misses tol (it
+    // can, by rounding, after the reduced system converged) continue with a
+    // tighter target.  Returns the number of RHS that did not reach tol.
+    int finish_report(const lqcd_solver_params &sp, lqcd_solve_info *info)
+    {
+        const double tol = tol_;
+        for (int attempt = 0; attempt < 4; ++attempt) {
             finish();
             pull_states();
             bool retry = false;
@@ -438,10 +483,11 @@ struct Solver {
                     retry = true;
                 }
             }
-            if (!retry || (cancel && *cancel)) break;
+            if (!retry || (cancel && *cancel) || attempt == 3) break;
             push_states();
             reliable_update();
             half2();
+            iterate(sp);
         }
         int failed = 0;
         for (int j = 0; j < nrhs; ++j) {
@@ -457,6 +503,14 @@ struct Solver {
             }
         }
         return failed;
+    }
+
+    // returns the number of RHS that did not reach tol
+    int run(const lqcd_solver_params &sp, lqcd_solve_info *info)
+    {
+        start(sp);
+        iterate(sp);
+        return finish_report(sp, info);
     }
 };
 
@@ -582,6 +636,159 @@ int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const 
         return solve_prec<F32, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
     case LQCD_PREC_MIXED_FP16:
         return solve_prec<F16, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+    default: throw Error{LQCD_EINVAL, "unknown precision"};
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched propagators on uneven lattices: every job is a 12-column point
+// source solve on its own lattice, gauge field and kappa.  After one eager
+// iteration (which also autotunes the kernels of every lattice size), the
+// iterations of all unfinished jobs are captured into one CUDA graph, one
+// branch per job and `chunk` iterations per branch, and that graph is
+// launched until every job has finished.  Inside the graph a right-hand side
+// that asks for an FP64 residual pauses; between launches the host runs the
+// FP64 updates of the jobs that asked and the updated right-hand sides
+// finish their iteration (ST_RESUME).  The graph is captured again whenever
+// the set of unfinished jobs shrinks.
+// ---------------------------------------------------------------------------
+template <class W, class E>
+struct BatchJob {
+    lqcd_pion_job *job = nullptr;
+    lqcd_lattice_s *lat = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t join = nullptr;
+    std::unique_ptr<Workspace> ws;
+    std::unique_ptr<Solver<W, E>> s;
+    bool active = true;
+    ~BatchJob()
+    {
+        s.reset();
+        ws.reset();
+        if (join) cudaEventDestroy(join);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+template <class W, class E>
+static int batch_t(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int chunk, cudaStream_t origin)
+{
+    std::vector<std::unique_ptr<BatchJob<W, E>>> J;
+    for (int k = 0; k < n; ++k) {
+        auto b = std::make_unique<BatchJob<W, E>>();
+        b->job = &jobs[k];
+        b->lat = jobs[k].lat;
+        LQCD_CUDA(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+        LQCD_CUDA(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+        auto it = b->lat->gauges.find(jobs[k].gauge_id);
+        if (it == b->lat->gauges.end()) throw Error{LQCD_EINVAL, "unknown gauge id in batch job " + std::to_string(k)};
+        GaugeSet &g = *it->second;
+        CloverSet &cl = clover_get(b->lat, g, jobs[k].dp.kappa, jobs[k].dp.csw, b->st);
+        b->ws = workspace_build(b->lat, 12, sp.precision, b->st, false);
+        b->s = std::make_unique<Solver<W, E>>(b->lat, *b->ws, g, cl, jobs[k].dp, 12, b->st);
+        point_sources(b->lat, jobs[k].src, b->s->b_e, b->s->b_o, b->st);
+        b->s->start(sp);
+        J.push_back(std::move(b));
+    }
+    // one eager iteration per job (autotunes the kernels outside any capture)
+    for (auto &b : J) {
+        b->s->half1();
+        b->s->pull_states();
+        if (b->s->any_status(ST_UPDATE)) b->s->reliable_update();
+        b->s->half2();
+    }
+    for (auto &b : J) {
+        b->s->set_resume(ST_RESUME);
+        LQCD_CUDA(cudaStreamSynchronize(b->st));
+    }
+    cudaEvent_t fork;
+    LQCD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto capture = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        LQCD_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+        LQCD_CUDA(cudaEventRecord(fork, origin));
+        for (auto &b : J) {
+            if (!b->active) continue;
+            LQCD_CUDA(cudaStreamWaitEvent(b->st, fork, 0));
+            for (int k = 0; k < chunk; ++k) {
+                b->s->half1();
+                b->s->half2();
+            }
+            LQCD_CUDA(cudaEventRecord(b->join, b->st));
+            LQCD_CUDA(cudaStreamWaitEvent(origin, b->join, 0));
+        }
+        LQCD_CUDA(cudaStreamEndCapture(origin, &graph));
+        LQCD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    };
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaEventDestroy(fork);
+    };
+    try {
+        int nactive = 0;
+        for (auto &b : J) {
+            b->active = !b->s->all_finished();
+            nactive += b->active;
+        }
+        int captured_for = -1;
+        const long max_chunks = (long(sp.maxiter) + 64) / chunk + 2;
+        for (long c = 0; c < max_chunks && nactive > 0; ++c) {
+            if (captured_for != nactive) {
+                capture();
+                captured_for = nactive;
+            }
+            LQCD_CUDA(cudaGraphLaunch(exec, origin));
+            LQCD_CUDA(cudaStreamSynchronize(origin));
+            for (auto &b : J) {
+                if (!b->active) continue;
+                b->s->pull_states();
+                if (b->s->any_status(ST_UPDATE)) {
+                    b->s->reliable_update();
+                    b->s->resumed_to_active();
+                }
+            }
+            nactive = 0;
+            for (auto &b : J) {
+                if (!b->active) continue;
+                b->s->pull_states();
+                b->active = !b->s->all_finished();
+                nactive += b->active;
+            }
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+    int failed_jobs = 0;
+    for (auto &b : J) {
+        b->s->set_resume(ST_ACTIVE);
+        const int T = b->lat->dims[3];
+        lqcd_pion_job &jb = *b->job;
+        int failed = b->s->finish_report(sp, jb.info);
+        Workspace &ws = *b->ws;  // w64 is free after the solve: it receives C(t)
+        pion_contract_soa(b->lat, b->s->x_e, b->s->x_o, jb.src[3], ws.w64.as<double>(), ws.partial.as<double>(),
+                          ws.counter.as<unsigned>(), b->st);
+        LQCD_CUDA(cudaMemcpyAsync(jb.corr, ws.w64.p, sizeof(double) * T, cudaMemcpyDeviceToHost, b->st));
+        LQCD_CUDA(cudaStreamSynchronize(b->st));
+        jb.status = failed ? LQCD_ENOCONV : LQCD_OK;
+        failed_jobs += failed != 0;
+    }
+    return failed_jobs;
+}
+
+int pion_batch(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int chunk, cudaStream_t origin)
+{
+    switch (sp.precision) {
+    case LQCD_PREC_FP64: return batch_t<F64, F64>(jobs, n, sp, chunk, origin);
+    case LQCD_PREC_MIXED_FP32: return batch_t<F32, F32>(jobs, n, sp, chunk, origin);
+    case LQCD_PREC_MIXED_FP16: return batch_t<F16, F32>(jobs, n, sp, chunk, origin);
     default: throw Error{LQCD_EINVAL, "unknown precision"};
     }
 }

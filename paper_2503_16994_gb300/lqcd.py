@@ -58,6 +58,11 @@ class SolveInfo(ctypes.Structure):
                 "true_resid": self.true_resid, "status": self.status}
 
 
+class PionJob(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_void_p), ("gauge_id", ctypes.c_int), ("dp", DiracParams), ("src", ctypes.c_int * 4),
+                ("corr", ctypes.POINTER(ctypes.c_double)), ("info", SolveInfo * 12), ("status", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -90,6 +95,7 @@ def load():
         "lqcd_pion_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip, vp, vp,
                            ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
         "lqcd_pion_contract": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp],
+        "lqcd_pion_corr_batch": [ctypes.POINTER(PionJob), ctypes.c_int, ctypes.POINTER(SolverParams), ctypes.c_int, vp],
         "lqcd_pion_contract_noalloc": [ip, vp, ctypes.c_int, vp, vp],
         "lqcd_serve_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)],
         "lqcd_serve_gauge": [vp, ip, vp, ip],
@@ -286,6 +292,26 @@ def pion_corr(lat, gauge_id, params: DiracParams, solver: SolverParams, src, dim
                                prop.ctypes.data_as(ctypes.c_void_p) if prop is not None else None, info, 0, None)
     _check(rc, allow=(OK, ENOCONV))
     return corr, prop, [i.as_dict() for i in info], rc
+
+
+def pion_corr_batch(jobs, solver: SolverParams, chunk=0):
+    """Batched propagators: jobs = [(lat, gauge_id, DiracParams, src, T), ...].
+
+    Returns (list of corr arrays, list of per-job info lists, list of statuses, rc)."""
+    arr = (PionJob * len(jobs))()
+    corrs = []
+    for k, (lat, gid, dp, src, T) in enumerate(jobs):
+        c = np.zeros(int(T))
+        corrs.append(c)
+        arr[k].lat = lat
+        arr[k].gauge_id = int(gid)
+        arr[k].dp = dp
+        for m in range(4):
+            arr[k].src[m] = int(src[m])
+        arr[k].corr = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = load().lqcd_pion_corr_batch(arr, len(jobs), ctypes.byref(solver), int(chunk), None)
+    _check(rc, allow=(OK, ENOCONV))
+    return corrs, [[i.as_dict() for i in a.info] for a in arr], [a.status for a in arr], rc
 
 
 def pion_contract(lat, prop, src_t, T=None, corr=None, stream=None):
