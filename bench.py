@@ -56,6 +56,23 @@ WORKLOAD = {
     "l2": "inputs larger than L2 (~10 GB working set vs 129 MB L2); no flush needed",
 }
 NOMINAL_HBM_GBS = 8000.0
+# DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
+# one ncu capture (profiles/hop_f16_12rhs_24c48_ncu_full.md, 24^3x48, 331776
+# sites per parity): 516.9 MB for hopclov and 784.9 MB for selfclov.  Every
+# operand is read once per site, so the traffic scales with the sites of a
+# launch.  Valid only for the kernel sources the capture was taken on
+# (digest below); otherwise the bench reports null.
+HOP_TRAFFIC = {"digest": "6fc636599ebd3b3e", "hop_f16_hopclov": 516.9e6 / 331776, "hop_f16_selfclov": 784.9e6 / 331776}
+KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh"]
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2503_16994_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 # Oracle cost model for the CPU baseline: one CGNR iteration costs two
 # full-lattice applications of D (D and D^dag).  The number of iterations is
 # taken as the normal-operator applications the GPU FP64 solver needs on this
@@ -141,7 +158,8 @@ def dist_setup():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group(backend="nccl" if _cuda_ok() else "gloo")
+        backend = os.environ.get("LQCD_DIST_BACKEND") or ("nccl" if _cuda_ok() else "gloo")
+        dist.init_process_group(backend=backend)
     return world, rank, local
 
 
@@ -164,7 +182,7 @@ def max_over_ranks(v, world):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda_ok() else "cpu")
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -444,6 +462,11 @@ def run_ours(args):
     achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
     peak, peak_kind = hbm_peak()
     launches = int(sum(v["launches"] for v in prof.values()))
+    traffic = None
+    if kernel_digest() == HOP_TRAFFIC["digest"] and hop_launches:
+        sites = inputs.volume(dims) // 2
+        tb = sum(v["timed_launches"] * HOP_TRAFFIC[k] * sites for k, v in hop.items() if k in HOP_TRAFFIC)
+        traffic = tb / hop_launches
     per_kernel = {k: {"launches": v["launches"], "ms": round(v["timed_ms"], 3),
                       "GB/s": round(v["timed_bytes"] / max(v["timed_ms"], 1e-9) / 1e6, 1)}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["timed_ms"])}
@@ -513,7 +536,9 @@ def run_ours(args):
                        "storage": "spinors FP16 + per-site FP32 scale, links FP16 recon-12, clover FP16; "
                                   "FP32 arithmetic; FP64 reliable updates and final residual"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "hop_f16_* (hopclov + selfclov)",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "hop_f16_* (hopclov + selfclov)",
+                         "traffic_source": "ncu capture at 24^3x48 scaled by sites (profiles/)",
+                         "algorithmic_bytes_per_launch": hop_bytes / hop_launches if hop_launches else None,
                          "peak_source": f"{peak_kind} hbm_gbs", "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS,
                          "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None},
             "dslash": dslash, "serving": serving, "batched": batch, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,

@@ -96,7 +96,7 @@ typedef struct {
  * (applications of the normal operator) per right-hand side.  precision:
  * LQCD_PREC_*.  inner_tol: the reliable-update factor delta (the residual is
  * recomputed in FP64 whenever the low-precision one has dropped by delta;
- * 0 selects the default 0.1).  nrhs: right-hand sides solved together
+ * 0 selects the default: 0.1 for FP16, 0.005 for FP32 inner vectors).  nrhs: right-hand sides solved together
  * (batched per launch), >= 1. */
 typedef struct {
     double tol;

@@ -423,7 +423,11 @@ struct Solver {
     // |b|, bhat, the FP64 residual of the zero start and the first z, p
     void start(const lqcd_solver_params &sp)
     {
-        delta_ = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : 0.1);
+        // default reliable-update factor per inner format (measured at
+        // 32^3 x 64): FP16 residuals drift, so they are refreshed every
+        // decade; FP32 ones hold until 5e-3
+        const double delta_default = std::is_same<W, F16>::value ? 0.1 : 0.005;
+        delta_ = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : delta_default);
         tol_ = sp.tol;
         prepare(0.5 * tol_, delta_, sp.maxiter);
         reliable_update();
