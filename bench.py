@@ -57,13 +57,13 @@ WORKLOAD = {
 }
 NOMINAL_HBM_GBS = 8000.0
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
-# one ncu capture (profiles/hop_f16_12rhs_24c48_ncu_full.md, 24^3x48, 331776
-# sites per parity): 516.9 MB for hopclov and 784.9 MB for selfclov.  Every
-# operand is read once per site, so the traffic scales with the sites of a
-# launch.  Valid only for the kernel sources the capture was taken on
-# (digest below); otherwise the bench reports null.
-HOP_TRAFFIC = {"digest": "6fc636599ebd3b3e", "hop_f16_hopclov": 516.9e6 / 331776, "hop_f16_selfclov": 784.9e6 / 331776}
-KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh"]
+# one ncu capture (profiles/hop_f16_12rhs_24c48_ncu_instmix.md, 24^3x48,
+# 331776 sites per parity, paired kernel): 509.8 MB for hopclov and 724.9 MB
+# for selfclov.  Every operand is read once per site, so the traffic scales
+# with the sites of a launch.  Valid only for the kernel sources the capture
+# was taken on (digest below); otherwise the bench reports null.
+HOP_TRAFFIC = {"digest": "c7f025e08e15b194", "hop_f16_hopclov": 509.83e6 / 331776, "hop_f16_selfclov": 724.85e6 / 331776}
+KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh", "hopp_inst.cuh"]
 
 
 def kernel_digest():

@@ -16,12 +16,6 @@ inline FastDiv make_fastdiv(unsigned d)
     return FastDiv{d, unsigned(m), l};
 }
 
-template <class S>
-static long padded_tiles(const FastHop<S> &f)
-{
-    return long((f.ntiles + f.swz - 1) / f.swz) * f.swz;
-}
-
 template <class S, int NR, int MODE, bool DAG, bool NORM>
 static void hopf_go(const FastHop<S> &f, cudaStream_t st)
 {
@@ -46,28 +40,10 @@ static void hopf_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cu
     }
 }
 
-template <class S, int MODE, bool DAG, bool NORM>
-static void hopp_go(const FastHop<S> &f, cudaStream_t st)
-{
-    const int ngr = (f.nrhs + 1) / 2;
-    const unsigned grid = unsigned(padded_tiles(f) * ((ngr + f.gpb - 1) / f.gpb));
-    if (f.minb >= 4)
-        hopp_kernel<S, MODE, DAG, NORM, 4><<<grid, kBlock, 0, st>>>(f);
-    else
-        hopp_kernel<S, MODE, DAG, NORM, 1><<<grid, kBlock, 0, st>>>(f);
-}
-
+// paired kernels: instantiated in hopp_f16.cu / hopp_f32.cu (own translation
+// units, so they compile in parallel with the rest)
 template <class S>
-static void hopp_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st)
-{
-    if (mode == HOP_CLOV) {
-        if (dag) norm ? hopp_go<S, HOP_CLOV, true, true>(f, st) : hopp_go<S, HOP_CLOV, true, false>(f, st);
-        else norm ? hopp_go<S, HOP_CLOV, false, true>(f, st) : hopp_go<S, HOP_CLOV, false, false>(f, st);
-    } else {
-        if (dag) norm ? hopp_go<S, SELF_CLOV, true, true>(f, st) : hopp_go<S, SELF_CLOV, true, false>(f, st);
-        else norm ? hopp_go<S, SELF_CLOV, false, true>(f, st) : hopp_go<S, SELF_CLOV, false, false>(f, st);
-    }
-}
+void hopp_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st);
 
 template <class S, int MODE, bool DAG, bool NORM>
 static void hopq_go(const FastHop<S> &f, int pf, cudaStream_t st)
@@ -173,7 +149,10 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
                     cand.push_back(HopShape{nr, gpb, 1, swz});
                 }
                 if (!std::is_same<S, F64>::value && nr == 1) cand.push_back(HopShape{nr, gpb, 6, 1});
-                if (nr == 0) cand.push_back(HopShape{nr, gpb, 4, 1});
+                if (nr == 0) {
+                    cand.push_back(HopShape{nr, gpb, 3, 1});
+                    cand.push_back(HopShape{nr, gpb, 4, 1});
+                }
             }
     }
     if (!std::is_same<S, F64>::value)

@@ -45,6 +45,13 @@ struct FastHop {
     Reduce red;
 };
 
+// tiles rounded up to whole super-tiles (the grid covers padded tiles)
+template <class S>
+inline long padded_tiles(const FastHop<S> &f)
+{
+    return long((f.ntiles + f.swz - 1) / f.swz) * f.swz;
+}
+
 // ---------------------------------------------------------------------------
 // float complex helpers on (re, im) pairs held in plain floats
 // ---------------------------------------------------------------------------
@@ -300,6 +307,159 @@ __device__ __forceinline__ void link_mul(const R u[18], R sc, const R hr[2][3], 
         }
 }
 
+// FP16 storage: the spin projection runs on the stored (re, im) half2 words
+// of each right-hand side, before conversion, so only the 12 projected reals
+// per right-hand side are converted to FP32 (rounding the projected sum to
+// FP16 adds an error of the order of the storage rounding).
+__device__ __forceinline__ __half2 h2_bits(unsigned b)
+{
+    __half2 h;
+    *reinterpret_cast<unsigned *>(&h) = b;
+    return h;
+}
+// u + s d for s = +-1
+template <int SGN> __device__ __forceinline__ __half2 h_addsg(__half2 u, __half2 d)
+{
+    if constexpr (SGN > 0) return __hadd2(u, d);
+    else return __hsub2(u, d);
+}
+// u + s i d = (u.re - s d.im, u.im + s d.re) for s = +-1
+template <int SGN> __device__ __forceinline__ __half2 h_addi(__half2 u, __half2 d)
+{
+    // half2 (lo, hi) = (-1, +1) or (+1, -1)
+    const __half2 m = h2_bits(SGN > 0 ? 0x3C00BC00u : 0xBC003C00u);
+    return __hfma2(__lowhigh2highlow(d), m, u);
+}
+
+// the 12 half2 (re, im) words of right-hand side j at site y and its scale
+__device__ __forceinline__ float load_words(const SpinorField<F16> &f, int j, int y, __half2 w[12])
+{
+    const uint4 *b = f.p + (long)j * 3 * f.stride + y;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint4 x = __ldg(b + k * f.stride);
+        const __half2 *h = reinterpret_cast<const __half2 *>(&x);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[4 * k + q] = h[q];
+    }
+    return __ldg(f.scale + (long)j * f.stride + y);
+}
+
+// h = up - S (i s_mu dn) (t: up - S dn) on half2 words; same cases as project_p
+template <int MU, int S>
+__device__ __forceinline__ void project_h(const __half2 v[12], __half2 h[2][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const __half2 u0 = v[c], u1 = v[3 + c], d0 = v[6 + c], d1 = v[9 + c];
+        if (MU == 0) {
+            h[0][c] = h_addi<-S>(u0, d1);
+            h[1][c] = h_addi<-S>(u1, d0);
+        } else if (MU == 1) {
+            h[0][c] = h_addsg<-S>(u0, d1);
+            h[1][c] = h_addsg<S>(u1, d0);
+        } else if (MU == 2) {
+            h[0][c] = h_addi<-S>(u0, d0);
+            h[1][c] = h_addi<S>(u1, d1);
+        } else {
+            h[0][c] = h_addsg<-S>(u0, d0);
+            h[1][c] = h_addsg<-S>(u1, d1);
+        }
+    }
+}
+
+// one direction of one right-hand side from FP16 words: projection on the
+// half2 words, unscaled link multiply, optional phase, then the per-site
+// scale folded into the accumulation (acc += sc g, as fmas).  Per lane this
+// is the arithmetic of the paired kernel, so every kernel shape gives the
+// same bits.
+template <bool DAGU>
+__device__ __forceinline__ void link_mul_ns(const float u[18], const float hr[2][3], const float hi[2][3],
+                                            float gr[2][3], float gi[2][3])
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (!DAGU)
+                    cmad(re, im, u[2 * (3 * a + b)], u[2 * (3 * a + b) + 1], hr[s][b], hi[s][b]);
+                else
+                    cmadc(re, im, u[2 * (3 * b + a)], u[2 * (3 * b + a) + 1], hr[s][b], hi[s][b]);
+            }
+            gr[s][a] = re;
+            gi[s][a] = im;
+        }
+}
+
+// acc += sc (1 + S g_mu) psi from g (cases of accumulate_f)
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_sc(float acc[24], const float gr[2][3], const float gi[2][3], float sc)
+{
+    const float ps = S > 0 ? sc : -sc, ms = -ps;  // S sc, -S sc
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[2 * c] = fmaf(gr[0][c], sc, acc[2 * c]);
+        acc[2 * c + 1] = fmaf(gi[0][c], sc, acc[2 * c + 1]);
+        acc[6 + 2 * c] = fmaf(gr[1][c], sc, acc[6 + 2 * c]);
+        acc[7 + 2 * c] = fmaf(gi[1][c], sc, acc[7 + 2 * c]);
+        float &l0r = acc[12 + 2 * c], &l0i = acc[13 + 2 * c], &l1r = acc[18 + 2 * c], &l1i = acc[19 + 2 * c];
+        if (MU == 0) {  // lower += S (i g1, i g0)
+            l0r = fmaf(gi[1][c], ms, l0r);
+            l0i = fmaf(gr[1][c], ps, l0i);
+            l1r = fmaf(gi[0][c], ms, l1r);
+            l1i = fmaf(gr[0][c], ps, l1i);
+        } else if (MU == 1) {  // lower += S (g1, -g0)
+            l0r = fmaf(gr[1][c], ps, l0r);
+            l0i = fmaf(gi[1][c], ps, l0i);
+            l1r = fmaf(gr[0][c], ms, l1r);
+            l1i = fmaf(gi[0][c], ms, l1i);
+        } else if (MU == 2) {  // lower += S (i g0, -i g1)
+            l0r = fmaf(gi[0][c], ms, l0r);
+            l0i = fmaf(gr[0][c], ps, l0i);
+            l1r = fmaf(gi[1][c], ps, l1r);
+            l1i = fmaf(gr[1][c], ms, l1i);
+        } else {  // lower -= S (g0, g1)
+            l0r = fmaf(gr[0][c], ms, l0r);
+            l0i = fmaf(gi[0][c], ms, l0i);
+            l1r = fmaf(gr[1][c], ms, l1r);
+            l1i = fmaf(gi[1][c], ms, l1i);
+        }
+    }
+}
+
+template <class S, int MU, int DIR, int SP>
+__device__ __forceinline__ void half_dir_rhs(const FastHop<S> &a, const float u[18], const __half2 w[12], float sc,
+                                             bool ph, float acc[24])
+{
+    __half2 hh[2][3];
+    project_h<MU, SP>(w, hh);
+    float hr[2][3], hi[2][3], gr[2][3], gi[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            hr[s][c] = __low2float(hh[s][c]);
+            hi[s][c] = __high2float(hh[s][c]);
+        }
+    link_mul_ns<(DIR < 0)>(u, hr, hi, gr, gi);
+    if (ph) {
+        const float pr = float(a.th_re[MU]), pi = DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]);
+        const float npi = DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float xr = gr[s][c], xi = gi[s][c];
+                gr[s][c] = fmaf(npi, xi, __fmul_rn(pr, xr));
+                gi[s][c] = fmaf(pi, xr, __fmul_rn(pr, xi));
+            }
+    }
+    accumulate_sc<MU, SP>(acc, gr, gi, sc);
+}
+
 // one direction for all NR right-hand sides of this thread
 template <class S, int NR, int MU, int DIR, int SG, typename R>
 __device__ __forceinline__ void dir_f(const FastHop<S> &a, const int (&jj)[NR], unsigned on, int i, int y, bool wrap,
@@ -312,6 +472,12 @@ __device__ __forceinline__ void dir_f(const FastHop<S> &a, const int (&jj)[NR], 
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         if (!((on >> r) & 1)) continue;
+        if constexpr (S::W == 8) {
+            __half2 w[12];
+            const float sc = load_words(a.in, jj[r], y, w);
+            half_dir_rhs<S, MU, DIR, SP>(a, u, w, sc, ph, acc[r]);
+            continue;
+        }
         R v[24];
         const R sc = load_raw<S, R>(a.in, jj[r], y, v);
         R hr[2][3], hi[2][3], gr[2][3], gi[2][3];
@@ -669,15 +835,94 @@ __device__ __forceinline__ void link_mul_p(const float u[18], float2 sc, const c
     }
 }
 
+// g = U h or U^dag h for both lanes (no scale)
+template <bool DAGU>
+__device__ __forceinline__ void link_mul_u(const float u[18], const cp h[2][3], cp g[2][3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cp acc0{bc(0.f), bc(0.f)}, acc1{bc(0.f), bc(0.f)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int k = DAGU ? 2 * (3 * b + a) : 2 * (3 * a + b);
+            const float2 ur = bc(u[k]), ui = bc(u[k + 1]), nui = bc(-u[k + 1]);
+            const float2 x1 = DAGU ? ui : nui, x2 = DAGU ? nui : ui;
+            acc0.r = p_fma(ur, h[0][b].r, acc0.r);
+            acc0.r = p_fma(x1, h[0][b].i, acc0.r);
+            acc0.i = p_fma(ur, h[0][b].i, acc0.i);
+            acc0.i = p_fma(x2, h[0][b].r, acc0.i);
+            acc1.r = p_fma(ur, h[1][b].r, acc1.r);
+            acc1.r = p_fma(x1, h[1][b].i, acc1.r);
+            acc1.i = p_fma(ur, h[1][b].i, acc1.i);
+            acc1.i = p_fma(x2, h[1][b].r, acc1.i);
+        }
+        g[0][a] = acc0;
+        g[1][a] = acc1;
+    }
+}
+
+// acc += sc (1 + S g_mu) psi from g; the cases of accumulate_p with every
+// add a packed fma by the per-site scale pair (sc, or nsc = -sc)
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_s(cp acc[12], const cp g[2][3], float2 sc, float2 nsc)
+{
+    const float2 ps = S > 0 ? sc : nsc, ms = S > 0 ? nsc : sc;  // S sc, -S sc
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = cp{p_fma(g[0][c].r, sc, acc[c].r), p_fma(g[0][c].i, sc, acc[c].i)};
+        acc[3 + c] = cp{p_fma(g[1][c].r, sc, acc[3 + c].r), p_fma(g[1][c].i, sc, acc[3 + c].i)};
+        cp &l0 = acc[6 + c], &l1 = acc[9 + c];
+        if (MU == 0) {  // lower += S (i g1, i g0)
+            l0 = cp{p_fma(g[1][c].i, ms, l0.r), p_fma(g[1][c].r, ps, l0.i)};
+            l1 = cp{p_fma(g[0][c].i, ms, l1.r), p_fma(g[0][c].r, ps, l1.i)};
+        } else if (MU == 1) {  // lower += S (g1, -g0)
+            l0 = cp{p_fma(g[1][c].r, ps, l0.r), p_fma(g[1][c].i, ps, l0.i)};
+            l1 = cp{p_fma(g[0][c].r, ms, l1.r), p_fma(g[0][c].i, ms, l1.i)};
+        } else if (MU == 2) {  // lower += S (i g0, -i g1)
+            l0 = cp{p_fma(g[0][c].i, ms, l0.r), p_fma(g[0][c].r, ps, l0.i)};
+            l1 = cp{p_fma(g[1][c].i, ps, l1.r), p_fma(g[1][c].r, ms, l1.i)};
+        } else {  // lower -= S (g0, g1)
+            l0 = cp{p_fma(g[0][c].r, ms, l0.r), p_fma(g[0][c].i, ms, l0.i)};
+            l1 = cp{p_fma(g[1][c].r, ms, l1.r), p_fma(g[1][c].i, ms, l1.i)};
+        }
+    }
+}
+
 template <class S, int MU, int DIR, int SG>
 __device__ __forceinline__ void dir_p(const FastHop<S> &a, int ja, int jb, int i, int y, bool wrap, cp acc[12])
 {
     constexpr int SP = DIR > 0 ? -SG : SG;
     float u[18];
     load_link18<S, float>(a.U, DIR > 0 ? a.parity : (a.parity ^ 1), MU, DIR > 0 ? i : y, u);
+    cp h[2][3], g[2][3];
+    if constexpr (S::W == 8) {
+        __half2 wa[12], wb[12], ha[2][3], hb[2][3];
+        const float sa = load_words(a.in, ja, y, wa), sb = load_words(a.in, jb, y, wb);
+        project_h<MU, SP>(wa, ha);
+        project_h<MU, SP>(wb, hb);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                h[s][c] = cp{make_float2(__low2float(ha[s][c]), __low2float(hb[s][c])),
+                             make_float2(__high2float(ha[s][c]), __high2float(hb[s][c]))};
+        link_mul_u<(DIR < 0)>(u, h, g);
+        if (wrap && ((a.theta_mask >> MU) & 1)) {
+            const float2 pr = bc(float(a.th_re[MU])), pi = bc(DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]));
+            const float2 npi = bc(DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]));
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const cp x = g[s][c];
+                    g[s][c] = cp{p_fma(npi, x.i, p_mul(pr, x.r)), p_fma(pi, x.r, p_mul(pr, x.i))};
+                }
+        }
+        accumulate_s<MU, SP>(acc, g, make_float2(sa, sb), make_float2(-sa, -sb));
+        return;
+    }
     cp v[12];
     const float2 sc = load_pair<S>(a.in, ja, jb, y, v);
-    cp h[2][3], g[2][3];
     project_p<MU, SP>(v, h);
     link_mul_p<(DIR < 0)>(u, sc, h, g);
     if (wrap && ((a.theta_mask >> MU) & 1)) {
@@ -933,6 +1178,11 @@ __device__ __forceinline__ void compute_dir(const FastHop<S> &a, const RawLink<S
     constexpr int SP = DIR > 0 ? -SG : SG;
     float u[18], v[24];
     decode_link<S>(rl, u);
+    if constexpr (S::W == 8) {
+        half_dir_rhs<S, MU, DIR, SP>(a, u, reinterpret_cast<const __half2 *>(rs.w), rs.sc,
+                                     wrap && ((a.theta_mask >> MU) & 1), acc);
+        return;
+    }
     decode_spinor<S>(rs, v);
     float hr[2][3], hi[2][3], gr[2][3], gi[2][3];
     project_f<MU, SP, float>(v, hr, hi);
