@@ -56,6 +56,13 @@ WORKLOAD = {
     "l2": "inputs larger than L2 (~10 GB working set vs 129 MB L2); no flush needed",
 }
 NOMINAL_HBM_GBS = 8000.0
+# FP32 (CUDA-core) peak derived from the unit counts and clock: 152 SMs x 128
+# FP32 lanes x 2 flop per fma x 2.07 GHz maximum SM clock.
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic flops per output site and RHS: hopping term 1320, clover
+# block pair 504, plus kappa scaling (hopclov, 24) or the combination with
+# the self term (selfclov, 48)
+HOP_FLOPS = {"hop_f16_hopclov": 1320 + 504 + 24, "hop_f16_selfclov": 1320 + 504 + 48}
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
 # one ncu capture (profiles/hop_f16_12rhs_24c48_ncu_instmix.md, 24^3x48,
 # 331776 sites per parity, paired kernel): 509.8 MB for hopclov and 724.9 MB
@@ -63,7 +70,7 @@ NOMINAL_HBM_GBS = 8000.0
 # with the sites of a launch.  Valid only for the kernel sources the capture
 # was taken on (digest below); otherwise the bench reports null.
 HOP_TRAFFIC = {"digest": "c7f025e08e15b194", "hop_f16_hopclov": 509.83e6 / 331776, "hop_f16_selfclov": 724.85e6 / 331776}
-KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh", "hopp_inst.cuh"]
+KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh", "hopp_inst.cuh", "hops.cuh"]
 
 
 def kernel_digest():
@@ -460,6 +467,9 @@ def run_ours(args):
     hop_launches = sum(v["timed_launches"] for v in hop.values())
     total_ms = sum(v["timed_ms"] for v in prof.values())
     achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
+    sites_h = inputs.volume(dims) // 2
+    hop_flops = sum(v["timed_launches"] * sites_h * nrhs * HOP_FLOPS[k] for k, v in hop.items() if k in HOP_FLOPS)
+    alu_achieved = hop_flops / (hop_ms / 1e3) / 1e12 if hop_ms > 0 else 0.0
     peak, peak_kind = hbm_peak()
     launches = int(sum(v["launches"] for v in prof.values()))
     traffic = None
@@ -540,7 +550,13 @@ def run_ours(args):
                          "traffic_source": "ncu capture at 24^3x48 scaled by sites (profiles/)",
                          "algorithmic_bytes_per_launch": hop_bytes / hop_launches if hop_launches else None,
                          "peak_source": f"{peak_kind} hbm_gbs", "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS,
-                         "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None},
+                         "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None,
+                         # the same kernels against the FP32 CUDA-core roof: at 12 RHS they sit at the
+                         # ridge (hopclov slightly above it, selfclov slightly below)
+                         "alu": {"achieved": alu_achieved, "peak": NOMINAL_FP32_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": alu_achieved / NOMINAL_FP32_TFLOPS,
+                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                                 "flops_per_site_rhs": HOP_FLOPS}},
             "dslash": dslash, "serving": serving, "batched": batch, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
             "fp64_gpu": fp64, "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
             "iters": {"inner_max": max(i["iters_inner"] for i in infos_last),

@@ -14,6 +14,37 @@ __global__ void __launch_bounds__(128) norm2_f64(VecArgs v, SpinorField<F64> x)
     reduce_finish(v.red, j, tile, v.ntiles, n2);
 }
 
+// Sum of the per-tile partials of each gated-in RHS (one block of 512
+// threads per RHS, four independent accumulators per thread, fixed order:
+// deterministic) and its operation.
+constexpr int kFinishThreads = 512;
+__global__ void __launch_bounds__(kFinishThreads) partial_finish_kernel(Reduce r, int ntiles, const RhsState *gate_st,
+                                                                       int gate)
+{
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    if (gate_st && gate_st[j].status != gate) return;
+    const double *p = r.partial + (long)j * ntiles;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int k = threadIdx.x;
+    for (; k + 3 * kFinishThreads < ntiles; k += 4 * kFinishThreads) {
+        t0 += p[k];
+        t1 += p[k + kFinishThreads];
+        t2 += p[k + 2 * kFinishThreads];
+        t3 += p[k + 3 * kFinishThreads];
+    }
+    for (; k < ntiles; k += kFinishThreads) t0 += p[k];
+    double t = block_sum((t0 + t1) + (t2 + t3), sh);
+    if (threadIdx.x == 0) apply_op(r, j, t);
+}
+
+void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st)
+{
+    ProfScope prof("norm_finish", double(nrhs) * ntiles * 8.0, st);
+    partial_finish_kernel<<<unsigned(nrhs), kFinishThreads, 0, st>>>(r, ntiles, gate_st, gate);
+    LQCD_CHECK_LAUNCH();
+}
+
 static unsigned grid_of(const VecArgs &v) { return unsigned(v.ntiles * v.nrhs); }
 
 template <class W, class E>

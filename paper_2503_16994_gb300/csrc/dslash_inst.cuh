@@ -44,6 +44,8 @@ static void hopf_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cu
 // units, so they compile in parallel with the rest)
 template <class S>
 void hopp_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st);
+// staged paired kernel (hops_f16.cu): pd directions of cp.async copies ahead
+void hops_dispatch(const FastHop<F16> &f, int pd, int mode, bool dag, bool norm, cudaStream_t st);
 
 template <class S, int MODE, bool DAG, bool NORM>
 static void hopq_go(const FastHop<S> &f, int pf, cudaStream_t st)
@@ -69,10 +71,18 @@ static void hopq_dispatch(const FastHop<S> &f, int pf, int mode, bool dag, bool 
 // nr in 1..3: NR right-hand sides per thread in scalar FP32/FP64 arithmetic;
 // nr == 0: two right-hand sides per thread in the lanes of packed FP32x2;
 // nr == -2, -4, -8: one right-hand side per thread, loads of 2, 4 or 8
-// directions issued before their arithmetic (FP16/FP32 only)
+// directions issued before their arithmetic (FP16/FP32 only);
+// nr == 12, 13: as nr == 0 with the words of 2 or 3 directions ahead staged
+// in shared memory by cp.async (FP16 only)
 template <class S>
 static void hopf_launch(const FastHop<S> &f, int nr, int mode, bool dag, bool norm, cudaStream_t st)
 {
+    if constexpr (std::is_same<S, F16>::value) {
+        if (nr >= 12) {
+            hops_dispatch(f, nr - 10, mode, dag, norm, st);
+            return;
+        }
+    }
     if constexpr (!std::is_same<S, F64>::value) {
         if (nr == 0) {
             hopp_dispatch<S>(f, mode, dag, norm, st);
@@ -112,7 +122,9 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
     const char *env_gpb = std::getenv("LQCD_HOP_GPB");
     if (env_nr || env_gpb) {
         int nr = env_nr ? std::atoi(env_nr) : 1, gpb = env_gpb ? std::atoi(env_gpb) : 1;
-        if (std::is_same<S, F64>::value || (nr != -2 && nr != -4 && nr != -8 && (nr < 0 || nr > 3))) nr = 1;
+        const bool staged = std::is_same<S, F16>::value && (nr == 12 || nr == 13);
+        if (std::is_same<S, F64>::value || (!staged && nr != -2 && nr != -4 && nr != -8 && (nr < 0 || nr > 3)))
+            nr = 1;
         const char *env_mb = std::getenv("LQCD_HOP_MINB");
         const char *env_sw = std::getenv("LQCD_HOP_SWZ");
         return HopShape{nr, std::max(gpb, 1), env_mb ? std::atoi(env_mb) : 1, env_sw ? std::max(1, std::atoi(env_sw)) : 1};
@@ -153,6 +165,15 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
                     cand.push_back(HopShape{nr, gpb, 3, 1});
                     cand.push_back(HopShape{nr, gpb, 4, 1});
                 }
+            }
+    }
+    if (std::is_same<S, F16>::value && f.nrhs >= 2) {
+        const int ngr = (f.nrhs + 1) / 2;
+        for (int gpb : {1, 2, 3, 6})
+            if (gpb <= ngr && (gpb == 1 || ngr % gpb == 0)) {
+                cand.push_back(HopShape{12, gpb, 3, 1});
+                cand.push_back(HopShape{12, gpb, 4, 1});
+                cand.push_back(HopShape{13, gpb, 3, 1});
             }
     }
     if (!std::is_same<S, F64>::value)
@@ -270,9 +291,12 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
         f.gpb = sh.gpb;
         f.minb = sh.minb;
         f.swz = sh.swz;
-        ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
-        hopf_launch<S>(f, sh.nr, mode, dag, norm, st);
-        LQCD_CHECK_LAUNCH();
+        {
+            ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
+            hopf_launch<S>(f, sh.nr, mode, dag, norm, st);
+            LQCD_CHECK_LAUNCH();
+        }
+        if (norm) launch_partial_finish(a.red, a.ntiles, a.nrhs, a.gate_st, a.gate, st);
         return;
     }
     ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);

@@ -666,7 +666,7 @@ __device__ __forceinline__ void hopf_group(const FastHop<S> &a, int tile, int g)
             }
             n2 = store_raw<S, R>(a.out, jj[r], i, res);
         }
-        if (NORM) reduce_finish(a.red, jj[r], tile, a.ntiles, n2);
+        if (NORM) reduce_partial(a.red, jj[r], tile, a.ntiles, n2);
     }
 }
 
@@ -888,6 +888,37 @@ __device__ __forceinline__ void accumulate_s(cp acc[12], const cp g[2][3], float
     }
 }
 
+// one direction of a pair of right-hand sides from their FP16 words (wa, wb,
+// scales sa, sb) and the decoded link u
+template <class S, int MU, int DIR, int SP>
+__device__ __forceinline__ void dir_words(const FastHop<S> &a, const float u[18], const __half2 wa[12],
+                                          const __half2 wb[12], float sa, float sb, bool wrap, cp acc[12])
+{
+    cp h[2][3], g[2][3];
+    __half2 ha[2][3], hb[2][3];
+    project_h<MU, SP>(wa, ha);
+    project_h<MU, SP>(wb, hb);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            h[s][c] = cp{make_float2(__low2float(ha[s][c]), __low2float(hb[s][c])),
+                         make_float2(__high2float(ha[s][c]), __high2float(hb[s][c]))};
+    link_mul_u<(DIR < 0)>(u, h, g);
+    if (wrap && ((a.theta_mask >> MU) & 1)) {
+        const float2 pr = bc(float(a.th_re[MU])), pi = bc(DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]));
+        const float2 npi = bc(DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]));
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const cp x = g[s][c];
+                g[s][c] = cp{p_fma(npi, x.i, p_mul(pr, x.r)), p_fma(pi, x.r, p_mul(pr, x.i))};
+            }
+    }
+    accumulate_s<MU, SP>(acc, g, make_float2(sa, sb), make_float2(-sa, -sb));
+}
+
 template <class S, int MU, int DIR, int SG>
 __device__ __forceinline__ void dir_p(const FastHop<S> &a, int ja, int jb, int i, int y, bool wrap, cp acc[12])
 {
@@ -896,29 +927,9 @@ __device__ __forceinline__ void dir_p(const FastHop<S> &a, int ja, int jb, int i
     load_link18<S, float>(a.U, DIR > 0 ? a.parity : (a.parity ^ 1), MU, DIR > 0 ? i : y, u);
     cp h[2][3], g[2][3];
     if constexpr (S::W == 8) {
-        __half2 wa[12], wb[12], ha[2][3], hb[2][3];
+        __half2 wa[12], wb[12];
         const float sa = load_words(a.in, ja, y, wa), sb = load_words(a.in, jb, y, wb);
-        project_h<MU, SP>(wa, ha);
-        project_h<MU, SP>(wb, hb);
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                h[s][c] = cp{make_float2(__low2float(ha[s][c]), __low2float(hb[s][c])),
-                             make_float2(__high2float(ha[s][c]), __high2float(hb[s][c]))};
-        link_mul_u<(DIR < 0)>(u, h, g);
-        if (wrap && ((a.theta_mask >> MU) & 1)) {
-            const float2 pr = bc(float(a.th_re[MU])), pi = bc(DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]));
-            const float2 npi = bc(DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]));
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const cp x = g[s][c];
-                    g[s][c] = cp{p_fma(npi, x.i, p_mul(pr, x.r)), p_fma(pi, x.r, p_mul(pr, x.i))};
-                }
-        }
-        accumulate_s<MU, SP>(acc, g, make_float2(sa, sb), make_float2(-sa, -sb));
+        dir_words<S, MU, DIR, SP>(a, u, wa, wb, sa, sb, wrap, acc);
         return;
     }
     cp v[12];
@@ -963,6 +974,54 @@ __device__ __forceinline__ void clov6_p(const float A[36], const cp *v, cp *o)
     }
 }
 
+// clover epilogue, store and norm partials of a pair of right-hand sides
+template <class S, int MODE, bool NORM>
+__device__ __forceinline__ void hopp_epilogue(const FastHop<S> &a, int tile, int i, bool valid, int ja, bool on_a,
+                                              int jb, bool on_b, const cp acc[12])
+{
+    double n2a = 0.0, n2b = 0.0;
+    if (valid) {
+        cp res[12];
+        const float2 cf = bc(float(a.coef));
+        if constexpr (MODE == HOP_CLOV) {
+            float A[36];
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
+                clov6_p(A, acc + 6 * blk, res + 6 * blk);
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) res[q] = cp{p_mul(cf, res[q].r), p_mul(cf, res[q].i)};
+        } else {
+            cp sv[12];
+            const float2 sc = load_pair<S>(a.self, ja, jb, i, sv);
+            if constexpr (S::W == 8) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) sv[q] = cp{p_mul(sv[q].r, sc), p_mul(sv[q].i, sc)};
+            }
+            float A[36];
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
+                clov6_p(A, sv + 6 * blk, res + 6 * blk);
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) res[q] = cp{p_fma(cf, acc[q].r, res[q].r), p_fma(cf, acc[q].i, res[q].i)};
+        }
+        float va[24], vb[24];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            va[2 * q] = res[q].r.x;
+            va[2 * q + 1] = res[q].i.x;
+            vb[2 * q] = res[q].r.y;
+            vb[2 * q + 1] = res[q].i.y;
+        }
+        if (on_a) n2a = store_raw<S, float>(a.out, ja, i, va);
+        if (on_b) n2b = store_raw<S, float>(a.out, jb, i, vb);
+    }
+    if (NORM) reduce_partial2(a.red, ja, on_a, jb, on_b, tile, a.ntiles, n2a, n2b);
+}
+
 template <class S, int MODE, bool DAG, bool NORM>
 __device__ __forceinline__ void hopp_group(const FastHop<S> &a, int tile, int g)
 {
@@ -1005,50 +1064,7 @@ __device__ __forceinline__ void hopp_group(const FastHop<S> &a, int tile, int g)
         w = t == 0;
         dir_p<S, 3, -1, SG>(a, ja, jb, i, i - (w ? -(a.L[3] - 1) * a.ot : a.ot), w, acc);
     }
-    double n2a = 0.0, n2b = 0.0;
-    if (valid) {
-        cp res[12];
-        const float2 cf = bc(float(a.coef));
-        if constexpr (MODE == HOP_CLOV) {
-            float A[36];
-#pragma unroll
-            for (int blk = 0; blk < 2; ++blk) {
-                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
-                clov6_p(A, acc + 6 * blk, res + 6 * blk);
-            }
-#pragma unroll
-            for (int q = 0; q < 12; ++q) res[q] = cp{p_mul(cf, res[q].r), p_mul(cf, res[q].i)};
-        } else {
-            cp sv[12];
-            const float2 sc = load_pair<S>(a.self, ja, jb, i, sv);
-            if constexpr (S::W == 8) {
-#pragma unroll
-                for (int q = 0; q < 12; ++q) sv[q] = cp{p_mul(sv[q].r, sc), p_mul(sv[q].i, sc)};
-            }
-            float A[36];
-#pragma unroll
-            for (int blk = 0; blk < 2; ++blk) {
-                load_clov_block<S, float>(a.clov, a.parity, i, blk, A);
-                clov6_p(A, sv + 6 * blk, res + 6 * blk);
-            }
-#pragma unroll
-            for (int q = 0; q < 12; ++q) res[q] = cp{p_fma(cf, acc[q].r, res[q].r), p_fma(cf, acc[q].i, res[q].i)};
-        }
-        float va[24], vb[24];
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            va[2 * q] = res[q].r.x;
-            va[2 * q + 1] = res[q].i.x;
-            vb[2 * q] = res[q].r.y;
-            vb[2 * q + 1] = res[q].i.y;
-        }
-        if (on_a) n2a = store_raw<S, float>(a.out, ja, i, va);
-        if (on_b) n2b = store_raw<S, float>(a.out, jb, i, vb);
-    }
-    if (NORM) {
-        if (on_a) reduce_finish(a.red, ja, tile, a.ntiles, n2a);
-        if (on_b) reduce_finish(a.red, jb, tile, a.ntiles, n2b);
-    }
+    hopp_epilogue<S, MODE, NORM>(a, tile, i, valid, ja, on_a, jb, on_b, acc);
 }
 
 // Block b handles tile b / nbt and pair groups [(b % nbt) gpb, ... + gpb).
@@ -1305,7 +1321,7 @@ __device__ __forceinline__ void hopq_item(const FastHop<S> &a, int tile, int j)
         }
         n2 = store_raw<S, float>(a.out, j, i, res);
     }
-    if (NORM) reduce_finish(a.red, j, tile, a.ntiles, n2);
+    if (NORM) reduce_partial(a.red, j, tile, a.ntiles, n2);
 }
 
 // Block b handles tile b / nbt and right-hand sides [(b % nbt) gpb, ... + gpb).

@@ -107,6 +107,42 @@ __device__ __forceinline__ void reduce_finish(const Reduce &r, int j, int tile, 
     }
 }
 
+// Block-wide sum of v written as this block's partial of RHS j, nothing
+// else: no fence, no atomic, so the block does not wait for its own stores.
+// The partials are summed by partial_finish_kernel (launched after the
+// producing kernel, same summation order as reduce_finish).  Must be called
+// by every thread of the block.
+__device__ __forceinline__ void reduce_partial(const Reduce &r, int j, int tile, int ntiles, double v)
+{
+    __shared__ double sh[32];
+    const double s = block_sum(v, sh);
+    if (threadIdx.x == 0) r.partial[(long)j * ntiles + tile] = s;
+}
+// the same for two right-hand sides at once (one pair of barriers)
+__device__ __forceinline__ void reduce_partial2(const Reduce &r, int ja, bool on_a, int jb, bool on_b, int tile,
+                                                int ntiles, double va, double vb)
+{
+    __shared__ double sh[2][32];
+    va = warp_sum(va);
+    vb = warp_sum(vb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[0][wid] = va;
+        sh[1][wid] = vb;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        va = warp_sum(lane < nw ? sh[0][lane] : 0.0);
+        vb = warp_sum(lane < nw ? sh[1][lane] : 0.0);
+        if (lane == 0) {
+            if (on_a) r.partial[(long)ja * ntiles + tile] = va;
+            if (on_b) r.partial[(long)jb * ntiles + tile] = vb;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // hopping term with fused epilogues
 //

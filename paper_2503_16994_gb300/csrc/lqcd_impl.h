@@ -206,6 +206,8 @@ template <class W>
 void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> w, SpinorField<W> r,
                       cudaStream_t st);
 void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st);
+// finishes the per-tile partials a hopping kernel wrote with reduce_partial
+void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st);
 template <class S, class C>
 void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
                          cudaStream_t st);
