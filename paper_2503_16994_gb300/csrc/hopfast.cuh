@@ -666,7 +666,10 @@ __device__ __forceinline__ void hopf_group(const FastHop<S> &a, int tile, int g)
             }
             n2 = store_raw<S, R>(a.out, jj[r], i, res);
         }
-        if (NORM) reduce_partial(a.red, jj[r], tile, a.ntiles, n2);
+        if (NORM) {
+            if constexpr (S::W == 2) reduce_partial<double>(a.red, jj[r], tile, a.ntiles, n2);
+            else reduce_partial<float>(a.red, jj[r], tile, a.ntiles, float(n2));  // n2 is an FP32 sum
+        }
     }
 }
 
@@ -1019,7 +1022,7 @@ __device__ __forceinline__ void hopp_epilogue(const FastHop<S> &a, int tile, int
         if (on_a) n2a = store_raw<S, float>(a.out, ja, i, va);
         if (on_b) n2b = store_raw<S, float>(a.out, jb, i, vb);
     }
-    if (NORM) reduce_partial2(a.red, ja, on_a, jb, on_b, tile, a.ntiles, n2a, n2b);
+    if (NORM) reduce_partial2(a.red, ja, on_a, jb, on_b, tile, a.ntiles, float(n2a), float(n2b));  // FP32 sums
 }
 
 template <class S, int MODE, bool DAG, bool NORM>
@@ -1321,7 +1324,7 @@ __device__ __forceinline__ void hopq_item(const FastHop<S> &a, int tile, int j)
         }
         n2 = store_raw<S, float>(a.out, j, i, res);
     }
-    if (NORM) reduce_partial(a.red, j, tile, a.ntiles, n2);
+    if (NORM) reduce_partial<float>(a.red, j, tile, a.ntiles, float(n2));  // FP16/FP32 only: an FP32 sum
 }
 
 // Block b handles tile b / nbt and right-hand sides [(b % nbt) gpb, ... + gpb).

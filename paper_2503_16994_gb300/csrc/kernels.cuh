@@ -107,24 +107,43 @@ __device__ __forceinline__ void reduce_finish(const Reduce &r, int j, int tile, 
     }
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Block-wide sum of v written as this block's partial of RHS j, nothing
 // else: no fence, no atomic, so the block does not wait for its own stores.
-// The partials are summed by partial_finish_kernel (launched after the
-// producing kernel, same summation order as reduce_finish).  Must be called
-// by every thread of the block.
-__device__ __forceinline__ void reduce_partial(const Reduce &r, int j, int tile, int ntiles, double v)
+// The partials are summed in FP64 by partial_finish_kernel (launched after
+// the producing kernel).  T is the type the block sums in: float for the
+// FP16/FP32 kernels, whose per-thread values are FP32 sums already (FP64 adds
+// are scarce on this GPU), double for the FP64 kernels.  Must be called by
+// every thread of the block.
+template <typename T>
+__device__ __forceinline__ void reduce_partial(const Reduce &r, int j, int tile, int ntiles, T v)
 {
-    __shared__ double sh[32];
-    const double s = block_sum(v, sh);
-    if (threadIdx.x == 0) r.partial[(long)j * ntiles + tile] = s;
+    __shared__ T sh[32];
+    v = warp_sum_t(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = warp_sum_t(lane < nw ? sh[lane] : T(0));
+        if (lane == 0) r.partial[(long)j * ntiles + tile] = double(v);
+    }
 }
-// the same for two right-hand sides at once (one pair of barriers)
+// the same for two right-hand sides at once (one pair of barriers), in FP32
 __device__ __forceinline__ void reduce_partial2(const Reduce &r, int ja, bool on_a, int jb, bool on_b, int tile,
-                                                int ntiles, double va, double vb)
+                                                int ntiles, float va, float vb)
 {
-    __shared__ double sh[2][32];
-    va = warp_sum(va);
-    vb = warp_sum(vb);
+    __shared__ float sh[2][32];
+    va = warp_sum_t(va);
+    vb = warp_sum_t(vb);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) {
@@ -134,11 +153,11 @@ __device__ __forceinline__ void reduce_partial2(const Reduce &r, int ja, bool on
     __syncthreads();
     if (wid == 0) {
         const int nw = (blockDim.x + 31) >> 5;
-        va = warp_sum(lane < nw ? sh[0][lane] : 0.0);
-        vb = warp_sum(lane < nw ? sh[1][lane] : 0.0);
+        va = warp_sum_t(lane < nw ? sh[0][lane] : 0.f);
+        vb = warp_sum_t(lane < nw ? sh[1][lane] : 0.f);
         if (lane == 0) {
-            if (on_a) r.partial[(long)ja * ntiles + tile] = va;
-            if (on_b) r.partial[(long)jb * ntiles + tile] = vb;
+            if (on_a) r.partial[(long)ja * ntiles + tile] = double(va);
+            if (on_b) r.partial[(long)jb * ntiles + tile] = double(vb);
         }
     }
 }
