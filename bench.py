@@ -83,7 +83,7 @@ def kernel_digest():
 # Oracle cost model for the CPU baseline: one CGNR iteration costs two
 # full-lattice applications of D (D and D^dag).  The number of iterations is
 # taken as the normal-operator applications the GPU FP64 solver needs on this
-# workload (measured on GB300); the oracle's unpreconditioned
+# workload (about 400 on GB300 at 32^3x64); the oracle's unpreconditioned
 # CGNR needs more, so the baseline over-states the oracle's speed.
 ORACLE_ITERS = 360
 

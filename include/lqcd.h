@@ -219,8 +219,8 @@ typedef struct {
  * columns iterate in the same CUDA graph (one branch per job, `chunk`
  * iterations per graph launch, 0 = 8), so the device runs all lattices at
  * once and the host issues one launch per chunk instead of one per kernel.
- * The benchmark spec's batched uneven solves; the paper solves one propagator at
- * a time (Sec. 4 example).  All jobs use sp (precision, tol, maxiter) and
+ * The paper solves one propagator at a time (Sec. 4 example); this batches
+ * uneven lattices into one device schedule.  All jobs use sp (precision, tol, maxiter) and
  * the device of their lattices (one device for the batch).  The call locks
  * every lattice involved and returns when all jobs are done; `stream` work
  * queued before the call completes first.
