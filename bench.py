@@ -64,8 +64,8 @@ NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # the self term (selfclov, 48)
 HOP_FLOPS = {"hop_f16_hopclov": 1320 + 504 + 24, "hop_f16_selfclov": 1320 + 504 + 48}
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
-# one ncu capture (profiles/hop_f16_12rhs_24c48_ncu_full.md, 24^3x48, 331776
-# sites per parity, staged paired kernel): 509.2 MB for hopclov and 722.9 MB
+# one ncu capture (24^3x48, 331776 sites per parity, staged paired kernel;
+# its summary is kept under profiles/): 509.2 MB for hopclov and 722.9 MB
 # for selfclov.  Every operand is read once per site, so the traffic scales
 # with the sites of a launch.  Valid only for the kernel sources the capture
 # was taken on (digest below); otherwise the bench reports null.
