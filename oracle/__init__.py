@@ -54,6 +54,7 @@ def _load():
                                     ctypes.c_double, ctypes.c_int, ip, dp]
         lib.oracle_cgnr.restype = ctypes.c_int
         lib.oracle_pion_contract.argtypes = [ip, dp, ctypes.c_int, dp]
+        lib.oracle_meson_contract.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_pion.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.c_double, ctypes.c_int, dp, dp, ip, dp]
         lib.oracle_pion.restype = ctypes.c_int
@@ -150,6 +151,17 @@ def pion_contract(dims, prop, src_t) -> np.ndarray:
     _load().oracle_pion_contract(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(prop), int(src_t),
                                  _dp(out))
     return out
+
+
+def meson_contract(dims, prop, src_t, gammas) -> np.ndarray:
+    """C_G(t) for each 4x4 spin matrix G in gammas[ng, 4, 4] from 12 propagator
+    columns prop[j, t, z, y, x, spin, colour]; complex array [ng, T]."""
+    prop, d = _c128(prop), _dims(dims)
+    g = _c128(np.asarray(gammas, dtype=np.complex128).reshape(-1, 4, 4))
+    out = np.zeros(2 * g.shape[0] * dims[3])
+    _load().oracle_meson_contract(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(prop), int(src_t), _dp(g),
+                                  int(g.shape[0]), _dp(out))
+    return out.view(np.complex128).reshape(g.shape[0], dims[3])
 
 
 def pion(dims, U, kappa, csw, src, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000, want_prop=False):

@@ -579,6 +579,72 @@ void oracle_pion_contract(const int *L, const double *prop, int src_t, double *c
         }
 }
 
+/* Meson two-point functions for arbitrary spin matrices (the contractions
+ * Sec. 3.3 leaves to the user: "any contraction" of the propagator), read as
+ * the connected correlator of O_G = psibar G psi with its conjugate at the
+ * source, using the gamma5-hermiticity S(x0, x) = g5 S(x, x0)^dag g5:
+ *     C_G(t) = - sum_xvec tr[ (G x 1) S(x) (Gbar x 1) g5 S(x)^dag g5 ],
+ *     Gbar = g_t G^dag g_t,  x = (xvec, src_t + t mod T),
+ * S(x) the 12 x 12 matrix S(x)[3 spin + colour][j] = prop[j][x][...].  For
+ * G = g5 this is the pion contraction above.  Written out as plain 12 x 12
+ * matrix products per site.  gammas: ng 4x4 complex row-major; corr: ng x T
+ * complex (re, im), t from the source slice. */
+void oracle_meson_contract(const int *L, const double *prop, int src_t, const double *gammas, int ng,
+                           double *corr)
+{
+    init_gamma();
+    const long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2];
+    const int T = L[3];
+    for (long k = 0; k < 2L * ng * T; ++k) corr[k] = 0;
+    static cplx S[12][12], R[12][12], A[12][12], B[12][12], Gs[4][4], Gb[4][4], tmp[4][4];
+    for (long s = 0; s < V; ++s) {
+        const int t = (int)(s / V3);
+        const int tr = ((t - src_t) % T + T) % T;
+        for (int i = 0; i < 12; ++i)
+            for (int j = 0; j < 12; ++j) {
+                const double *q = prop + 24 * (V * j + s) + 2 * i;
+                S[i][j] = q[0] + I * q[1];
+            }
+        /* R = g5 S^dag g5 (g5 = G[4] acts on the spin index) */
+        for (int i = 0; i < 12; ++i)
+            for (int j = 0; j < 12; ++j) R[i][j] = G[4][i / 3][i / 3] * conj(S[j][i]) * G[4][j / 3][j / 3];
+        for (int g = 0; g < ng; ++g) {
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b)
+                    Gs[a][b] = gammas[2 * (16 * g + 4 * a + b)] + I * gammas[2 * (16 * g + 4 * a + b) + 1];
+            /* Gbar = g_t G^dag g_t */
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) {
+                    cplx c = 0;
+                    for (int l = 0; l < 4; ++l) c += G[3][a][l] * conj(Gs[b][l]);
+                    tmp[a][b] = c;
+                }
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) {
+                    cplx c = 0;
+                    for (int l = 0; l < 4; ++l) c += tmp[a][l] * G[3][l][b];
+                    Gb[a][b] = c;
+                }
+            /* A = (G x 1) S, B = (Gbar x 1) R, value = -tr(A B) */
+            for (int i = 0; i < 12; ++i)
+                for (int j = 0; j < 12; ++j) {
+                    cplx ca = 0, cb = 0;
+                    for (int l = 0; l < 4; ++l) {
+                        ca += Gs[i / 3][l] * S[3 * l + i % 3][j];
+                        cb += Gb[i / 3][l] * R[3 * l + i % 3][j];
+                    }
+                    A[i][j] = ca;
+                    B[i][j] = cb;
+                }
+            cplx v = 0;
+            for (int i = 0; i < 12; ++i)
+                for (int k = 0; k < 12; ++k) v += A[i][k] * B[k][i];
+            corr[2 * (g * T + tr)] -= creal(v);
+            corr[2 * (g * T + tr) + 1] -= cimag(v);
+        }
+    }
+}
+
 /* Solves the 12 point sources at src = (x, y, z, t) and contracts them.
  * prop (may be NULL) receives the 12 columns [j][site][12] complex; iters and
  * resid (may be NULL) receive per-column counts and true residuals.  Returns

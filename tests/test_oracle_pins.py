@@ -356,6 +356,60 @@ def test_pion_contract_sums_all_columns():
     assert np.count_nonzero(c1) == 1 and c1[3] > 0
 
 
+def clifford16():
+    """The 16 products 1, g_mu, g_mu g_nu (mu<nu), g_mu g_nu g_rho (mu<nu<rho),
+    g5 of the chiral basis built in this file; orthonormal: tr(A B^dag) = 4 delta."""
+    g = BASIS
+    out = [np.eye(4, dtype=complex)] + list(g)
+    out += [g[m] @ g[n] for m in range(4) for n in range(m + 1, 4)]
+    out += [g[m] @ g[n] @ g[r] for m in range(4) for n in range(m + 1, 4) for r in range(n + 1, 4)]
+    out.append(G5)
+    return np.array(out)
+
+
+def _random_prop(dims, seed):
+    rng = np.random.default_rng(seed)
+    shape = (12, dims[3], dims[2], dims[1], dims[0], 4, 3)
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def test_meson_gamma5_channel_is_the_pion():
+    """For G = g5, Gbar = g_t g5 g_t = -g5 and the trace collapses to sum |S|^2
+    for any 12-column array: the meson contraction must equal the (separately
+    pinned) pion contraction and be real."""
+    dims = (2, 4, 2, 6)
+    prop = _random_prop(dims, 3)
+    c = oracle.meson_contract(dims, prop, 2, [G5])
+    p = oracle.pion_contract(dims, prop, 2)
+    assert rel(c[0].real, p) < 1e-13
+    assert np.max(np.abs(c[0].imag)) < 1e-13 * np.max(p)
+
+
+def test_meson_fierz_completeness():
+    """Completeness of the Clifford basis, sum_A (G_A)_ab (G_A^dag)_cd =
+    4 delta_ad delta_bc, turns the sum over all 16 channels into
+    -4 sum_xvec tr_c[ tr_s(S g_t) tr_s(g_t g5 S^dag g5) ], computed here with
+    einsum on the propagator directly.  Any transposed, conjugated or
+    misordered factor in the contraction breaks it."""
+    basis = clifford16()
+    gram = np.einsum("aij,bij->ab", basis, basis.conj())
+    assert np.allclose(gram, 4 * np.eye(16), atol=1e-14)
+    dims = (2, 2, 4, 4)
+    src_t = 3
+    prop = _random_prop(dims, 5)
+    c = oracle.meson_contract(dims, prop, src_t, basis)
+    gt = BASIS[3]
+    g5d = np.diag(G5).real
+    # S[t, site, alpha, a, beta, b] = prop[3 beta + b][t, site][alpha, a]
+    S = prop.reshape(4, 3, dims[3], -1, 4, 3).transpose(2, 3, 4, 5, 0, 1)
+    M = np.einsum("tsAaBb,BA->tsab", S, gt)                      # tr_s(S g_t)
+    Tm = np.einsum("A,tsBbAa,B->tsAaBb", g5d, S.conj(), g5d)     # g5 S^dag g5
+    N = np.einsum("AB,tsBaAb->tsab", gt, Tm)                      # tr_s(g_t T)
+    rhs_t = -4 * np.einsum("tsab,tsba->t", M, N)
+    rhs = np.array([rhs_t[(src_t + t) % dims[3]] for t in range(dims[3])])
+    assert rel(c.sum(axis=0), rhs) < 1e-13
+
+
 # --------------------------------------------------------------------------
 # the input generator (shared by both sides)
 # --------------------------------------------------------------------------
