@@ -265,6 +265,42 @@ def dslash_measure(lqcd, lat, gid, dp, dims, legs=DSLASH_LEGS):
     return out
 
 
+def meson_measure(lqcd, lat, dims, repeat=5):
+    """Times lqcd_meson_contract for the 16 Clifford spin matrices on a
+    12-column array of the workload's size (values do not change the cost).
+    FP64 throughout: per site 256 terms of 9 complex conj-products and one
+    complex coefficient, 80 flop each; the 12 columns (2304 B per site) are
+    read from HBM once."""
+    import torch
+    T = dims[3]
+    V = int(np.prod(dims))
+    # chiral basis: g_k = [[0, -i s_k], [i s_k, 0]], g_t = [[0, -1], [-1, 0]]
+    pauli = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]], complex)]
+    z, i2 = np.zeros((2, 2)), np.eye(2)
+    g = [np.block([[z, -1j * s], [1j * s, z]]) for s in pauli] + [np.block([[z, -i2], [-i2, z]])]
+    gam = [np.eye(4, dtype=complex)] + g + [g[m] @ g[n] for m in range(4) for n in range(m + 1, 4)]
+    gam += [g[m] @ g[n] @ g[r] for m in range(4) for n in range(m + 1, 4) for r in range(n + 1, 4)]
+    gam.append(g[3] @ g[0] @ g[1] @ g[2])
+    prop = torch.empty((12 * V * 12,), dtype=torch.complex128, device="cuda")
+    prop.real.normal_()
+    prop.imag.normal_()
+    c = torch.zeros((16, T), dtype=torch.complex128, device="cuda")
+    lqcd.meson_contract(lat, prop, 0, gam, corr=c)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(repeat):
+        lqcd.meson_contract(lat, prop, 0, gam, corr=c)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / repeat
+    del prop
+    torch.cuda.empty_cache()
+    flops = 256 * 80.0 * V
+    return {"channels": 16, "ms": ms, "GB/s": 2304.0 * V / (ms / 1e3) / 1e9,
+            "fp64_TFLOP/s": flops / (ms / 1e3) / 1e12, "flop_per_site": 256 * 80, "arithmetic": "FP64"}
+
+
 def run_dslash_only(args):
     """Standalone Dslash timing on a chosen lattice (used for ncu captures)."""
     import torch
@@ -529,6 +565,7 @@ def run_ours(args):
                 "true_resid_max": max(i["true_resid"] for i in infos64)}
 
     dslash = None if args.no_dslash else dslash_measure(lqcd, lat, gid, dp, dims)
+    meson = None if (args.no_meson or rank != 0) else meson_measure(lqcd, lat, dims)
     serving = None if (args.serve_requests <= 0 or rank != 0) else serving_measure(lqcd, args.serve_requests)
     batch = None if (args.no_batch or rank != 0) else batch_measure(lqcd)
 
@@ -557,7 +594,7 @@ def run_ours(args):
                                  "frac": alu_achieved / NOMINAL_FP32_TFLOPS,
                                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                                  "flops_per_site_rhs": HOP_FLOPS}},
-            "dslash": dslash, "serving": serving, "batched": batch, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "dslash": dslash, "meson": meson, "serving": serving, "batched": batch, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
             "fp64_gpu": fp64, "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
             "iters": {"inner_max": max(i["iters_inner"] for i in infos_last),
                       "outer_max": max(i["iters_outer"] for i in infos_last),
@@ -615,6 +652,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-meson", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
     ap.add_argument("--dslash-only", action="store_true", help="time only the Dslash on --lattice")
     ap.add_argument("--lattice", default="32,32,32,64")

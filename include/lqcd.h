@@ -236,6 +236,26 @@ int lqcd_pion_corr_batch(lqcd_pion_job *jobs, int njobs, const lqcd_solver_param
 int lqcd_pion_contract(lqcd_lattice lat, const double *prop, int src_t, double *corr, int flags,
                        void *stream);
 
+/* Meson two-point functions for arbitrary spin matrices (the "any
+ * contraction" of a propagator, Sec. 3.3): for each of the ng 4x4 complex
+ * matrices G (gammas: ng * 16 complex = 32 ng doubles, row-major, chiral
+ * basis of lqcd_dirac_apply, always a host pointer),
+ *     corr[g][t] = - sum_xvec tr[ (G x 1) S(x) (Gbar x 1) g5 S(x)^dag g5 ],
+ *     Gbar = g_t G^dag g_t,  x = (xvec, src_t + t mod T),
+ * the connected correlator of psibar G psi with its conjugate at the source
+ * (S(x0, x) = g5 S(x, x0)^dag g5).  S(x)[3 spin + colour][j] is column j of
+ * prop (12 * 24 V doubles, host layout, source on slice src_t).  corr:
+ * ng * T complex values (2 ng T doubles, re then im), t counted from the
+ * source slice.  G = g5 gives the pion contraction.  Host pointers for prop
+ * and corr, or device pointers with LQCD_DEVICE_PTRS (then on `stream`).
+ * FP64 throughout; a G with one nonzero per row (the 16 Clifford basis
+ * elements) costs 16 terms of 9 complex products per site, a dense G 256.
+ * Returns LQCD_EINVAL for null pointers, src_t outside the lattice, ng
+ * outside 1..LQCD_MESON_MAX_GAMMAS or non-finite entries of gammas. */
+#define LQCD_MESON_MAX_GAMMAS 64
+int lqcd_meson_contract(lqcd_lattice lat, const double *prop, int src_t, const double *gammas, int ng, double *corr,
+                        int flags, void *stream);
+
 /* ---------------- launch accounting and timing ------------------------- */
 
 /* Per-kernel statistics since the last lqcd_profile_reset.  launches and

@@ -2,6 +2,7 @@
 // error reporting.  No call aborts: every failure becomes a status code with
 // a thread-local message.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -341,6 +342,37 @@ int lqcd_pion_contract(lqcd_lattice lat, const double *prop, int src_t, double *
     }
     pion_contract_aos(lat, pd, src_t, cd, lat->red_partial.as<double>(), lat->red_counter.as<unsigned>(), st);
     if (!(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(corr, cd, sizeof(double) * T, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_meson_contract(lqcd_lattice lat, const double *prop, int src_t, const double *gammas, int ng, double *corr,
+                        int flags, void *stream)
+{
+    if (!lat || !prop || !gammas || !corr) return fail(LQCD_EINVAL, "null argument");
+    if (src_t < 0 || src_t >= lat->dims[3]) return fail(LQCD_EINVAL, "source time outside the lattice");
+    if (ng < 1 || ng > LQCD_MESON_MAX_GAMMAS) return fail(LQCD_EINVAL, "ng must be in 1..LQCD_MESON_MAX_GAMMAS");
+    for (int k = 0; k < 32 * ng; ++k)
+        if (!std::isfinite(gammas[k])) return fail(LQCD_EINVAL, "gammas must be finite");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int T = lat->dims[3];
+    const size_t pbytes = sizeof(double) * 24 * (size_t)lat->V * 12;
+    const size_t cbytes = sizeof(double) * 2 * (size_t)ng * T;
+    const double *pd = prop;
+    double *cd = corr;
+    if (!(flags & LQCD_DEVICE_PTRS)) {
+        lat->staging.ensure(pbytes);
+        lat->staging2.ensure(cbytes);
+        LQCD_CUDA(cudaMemcpyAsync(lat->staging.p, prop, pbytes, cudaMemcpyHostToDevice, st));
+        pd = lat->staging.as<const double>();
+        cd = lat->staging2.as<double>();
+    }
+    meson_contract(lat, pd, src_t, gammas, ng, cd, st);
+    if (!(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(corr, cd, cbytes, cudaMemcpyDeviceToHost, st));
     LQCD_CUDA(cudaStreamSynchronize(st));
     return LQCD_OK;
     API_CATCH

@@ -189,6 +189,9 @@ void pion_contract_soa(lqcd_lattice_s *lat, SpinorField<F64> even, SpinorField<F
 // corr[t] from 12 host-layout columns already on the device
 void pion_contract_aos(lqcd_lattice_s *lat, const double *prop_dev, int src_t, double *corr_dev,
                        double *partial, unsigned *counter, cudaStream_t st);
+// corr[g][t] (complex) for ng host 4x4 spin matrices, 12 host-layout columns on the device (meson.cu)
+void meson_contract(lqcd_lattice_s *lat, const double *prop_dev, int src_t, const double *gammas, int ng,
+                    double *corr_dev, cudaStream_t st);
 
 // hopping kernels (dslash_f64.cu, dslash_f32.cu, dslash_f16.cu)
 template <class S, class L, class C>

@@ -95,6 +95,7 @@ def load():
         "lqcd_pion_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip, vp, vp,
                            ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
         "lqcd_pion_contract": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp],
+        "lqcd_meson_contract": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp],
         "lqcd_pion_corr_batch": [ctypes.POINTER(PionJob), ctypes.c_int, ctypes.POINTER(SolverParams), ctypes.c_int, vp],
         "lqcd_pion_contract_noalloc": [ip, vp, ctypes.c_int, vp, vp],
         "lqcd_serve_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)],
@@ -328,6 +329,27 @@ def pion_contract(lat, prop, src_t, T=None, corr=None, stream=None):
     c = np.zeros(T)
     _check(load().lqcd_pion_contract(lat, p.ctypes.data_as(ctypes.c_void_p), int(src_t),
                                      c.ctypes.data_as(ctypes.c_void_p), 0, None))
+    return c
+
+
+def meson_contract(lat, prop, src_t, gammas, T=None, corr=None, stream=None):
+    """C_G(t) for each 4x4 spin matrix G in gammas[ng, 4, 4] from 12 host-layout
+    propagator columns (numpy or CUDA tensor); complex [ng, T].  With a CUDA
+    `prop`, `corr` must be a complex128 (or float64 [ng, T, 2]) CUDA tensor."""
+    g = np.ascontiguousarray(np.asarray(gammas, dtype=np.complex128).reshape(-1, 4, 4))
+    gp = g.ctypes.data_as(ctypes.c_void_p)
+    if _is_cuda_tensor(prop):
+        n = prop.numel() * (2 if prop.is_complex() else 1)
+        if corr is None:
+            raise ValueError("device mode needs a CUDA tensor `corr` of ng * T complex values")
+        _check(load().lqcd_meson_contract(lat, _dev_ptr(prop, n), int(src_t), gp, int(g.shape[0]),
+                                          ctypes.c_void_p(corr.data_ptr()), DEVICE_PTRS, _stream_of(prop, stream)))
+        return corr
+    p = _host(prop)
+    T = p.shape[1] if T is None else T
+    c = np.zeros((g.shape[0], T), dtype=np.complex128)
+    _check(load().lqcd_meson_contract(lat, p.ctypes.data_as(ctypes.c_void_p), int(src_t), gp, int(g.shape[0]),
+                                      c.ctypes.data_as(ctypes.c_void_p), 0, None))
     return c
 
 

@@ -57,6 +57,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.lqcd_cg_solve(None, 0, None, None, None, None, 1, None, 0, None) == lqcd.EINVAL
     assert lib.lqcd_pion_corr(None, 0, None, None, None, None, None, None, 0, None) == lqcd.EINVAL
     assert lib.lqcd_pion_contract(None, None, 0, None, 0, None) == lqcd.EINVAL
+    assert lib.lqcd_meson_contract(None, None, 0, None, 1, None, 0, None) == lqcd.EINVAL
     assert lqcd.last_error() != ""
     assert lib.lqcd_lattice_destroy(None) == lqcd.OK
 
