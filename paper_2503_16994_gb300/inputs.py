@@ -201,6 +201,29 @@ def point_source(dims, src, spin: int, colour: int) -> np.ndarray:
     return eta
 
 
+def noise_source(dims, t0: int, seed: int, kind: str = "gauss") -> np.ndarray:
+    """Stochastic source on time slice t0, zero elsewhere, shape (T, Z, Y, X, 4, 3).
+
+    ``kind = "gauss"``: every spin-colour component of the slice complex
+    Gaussian, re and im ~ N(0, 1/2) (E|eta|^2 = 1).  ``kind = "z2"``:
+    (+-1 +- i)/sqrt(2) from the signs of two normals.  Either way
+    E[eta_a eta_b^*] = delta_ab, so sum_x |D^-1 eta|^2 on slice t estimates
+    the pion correlator summed over all source points of slice t0.
+    """
+    lx, ly, lz, lt = dims
+    cnt = lx * ly * lz * 12
+    g = normals(seed, 0, 2 * cnt).reshape(cnt, 2)
+    if kind == "gauss":
+        vals = (g[:, 0] + 1j * g[:, 1]) / np.sqrt(2.0)
+    elif kind == "z2":
+        vals = (np.sign(g[:, 0]) + 1j * np.sign(g[:, 1])) / np.sqrt(2.0)
+    else:
+        raise ValueError("kind must be 'gauss' or 'z2'")
+    eta = np.zeros((lt, lz, ly, lx, 4, 3), dtype=np.complex128)
+    eta[t0] = vals.reshape(lz, ly, lx, 4, 3)
+    return eta
+
+
 def gauge_transform(dims, seed: int, eps: float = 2.0) -> np.ndarray:
     """Random SU(3) matrix per site, g(x) = exp(i eps H(x)), shape (T, Z, Y, X, 3, 3)."""
     lx, ly, lz, lt = dims

@@ -147,3 +147,34 @@ def test_meson_full_size(lq, dims):
         lq.lattice_destroy(lat)
         del prop
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16"])
+def test_noise_source_propagator(lq, prec):
+    """Noise-source propagators (Sec. 3.3 propagator! with random sources):
+    lqcd_cg_solve on a Z2 source on one time slice, against the oracle's
+    solve of the same source, and the one-end estimator sum_x |psi|^2 per
+    slice through lqcd_pion_contract (the column in slot 0, the others zero)."""
+    dims, kappa, csw = (6, 4, 4, 8), 0.125, 1.4
+    t0 = 3
+    U = inputs.gauge_field(dims, 0.3, seed=9)
+    eta = inputs.noise_source(dims, t0, seed=17, kind="z2")
+    x_ref, it, res, ok = oracle.cgnr(dims, U, kappa, csw, eta, tol=1e-13)
+    assert ok
+    lat = lq.lattice_create(dims)
+    try:
+        gid = lq.gauge_upload(lat, U)
+        x, info, rc = lq.cg_solve(lat, gid, lq.dirac_params(kappa, csw),
+                                  lq.solver_params(tol=1e-10, maxiter=5000, precision=prec), eta)
+        assert rc == lq.OK, info
+        r = eta - oracle.dirac(dims, U, kappa, csw, x)
+        assert np.linalg.norm(r) / np.linalg.norm(eta) <= 1e-10
+        assert rel(x, x_ref) <= 1e-8
+        cols = np.zeros((12,) + x.shape, dtype=np.complex128)
+        cols[0] = x
+        c = lq.pion_contract(lat, cols, t0)
+    finally:
+        lq.lattice_destroy(lat)
+    want = np.sum(np.abs(x_ref) ** 2, axis=(1, 2, 3, 4, 5))
+    want = np.array([want[(t0 + t) % dims[3]] for t in range(dims[3])])
+    assert np.all(np.abs(c - want) <= 1e-8 * want)

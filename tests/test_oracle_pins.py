@@ -414,6 +414,19 @@ def test_meson_fierz_completeness():
 # the input generator (shared by both sides)
 # --------------------------------------------------------------------------
 
+def test_noise_source_generator():
+    dims = (8, 8, 8, 6)
+    for kind in ("gauss", "z2"):
+        eta = inputs.noise_source(dims, 4, seed=3, kind=kind)
+        assert np.count_nonzero(np.delete(eta, 4, axis=0)) == 0
+        m2 = np.mean(np.abs(eta[4]) ** 2)
+        assert abs(m2 - 1.0) < 0.03, (kind, m2)
+        assert abs(np.mean(eta[4])) < 0.03
+        assert np.array_equal(eta, inputs.noise_source(dims, 4, seed=3, kind=kind))
+    z2 = inputs.noise_source(dims, 4, seed=3, kind="z2")[4]
+    assert np.allclose(np.abs(z2), 1.0, atol=1e-15)
+
+
 def test_splitmix64_reference_outputs():
     vals = [int(l) for l in open(os.path.join(HERE, "golden", "splitmix64_seed1234567.txt"))
             if l.strip() and not l.startswith("#")]
