@@ -1,5 +1,6 @@
 // Instantiations of the staged paired hopping kernel (FP16 storage).
 #include <mutex>
+#include <set>
 
 #include "hops.cuh"
 #include "lqcd_impl.h"
@@ -11,12 +12,24 @@ static void hops_launch(const FastHop<F16> &f, unsigned grid, cudaStream_t st)
 {
     constexpr int smem = stage_bytes(PD);
     // the stage plus the kernel's static shared memory (reductions) exceeds
-    // the 48 KB a block gets without opting in
-    static std::once_flag once;
-    std::call_once(once, [] {
-        LQCD_CUDA(cudaFuncSetAttribute(hops_kernel<MODE, DAG, NORM, MINB, PD>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    });
+    // the 48 KB a block gets without opting in; the opt-in is a per-device
+    // attribute, set the first time the kernel runs on each device (the
+    // autotuner's eager launches, before any stream capture)
+    static std::mutex mu;
+    static std::set<int> opted;
+    int dev = 0;
+    LQCD_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (opted.insert(dev).second) {
+            const cudaError_t e = cudaFuncSetAttribute(hops_kernel<MODE, DAG, NORM, MINB, PD>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) {
+                opted.erase(dev);
+                LQCD_CUDA(e);
+            }
+        }
+    }
     hops_kernel<MODE, DAG, NORM, MINB, PD><<<grid, kBlock, smem, st>>>(f);
 }
 
