@@ -285,15 +285,19 @@ int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count);
 /* Autotuning decisions taken so far in this process, as a JSON array
  * written into buf (len bytes, NUL-terminated).  Each entry names a kernel,
  * the problem (sites per parity, right-hand sides) and the chosen shape
- * with its time: rhs_per_thread (1..3: right-hand sides per thread in
- * scalar arithmetic; 0: two right-hand sides in the lanes of packed FP32x2
- * instructions; -2/-4/-8: one right-hand side with the loads of 2/4/8
- * directions issued ahead), rhs_groups_per_block (groups run in sequence by
- * one block), min_blocks_per_sm (register cap), tiles_per_supertile (block
- * order) and block (threads).  The hopping kernels time these candidates on
- * their first launch for each (sites, nrhs, format, mode) and keep the
- * fastest; the environment variables LQCD_HOP_NR, LQCD_HOP_GPB,
- * LQCD_HOP_MINB and LQCD_HOP_SWZ force a shape instead.  Returns LQCD_EINVAL
+ * with its time: variant ("scalar": 1..3 right-hand sides per thread in
+ * scalar arithmetic; "paired": two right-hand sides in the lanes of packed
+ * FP32x2 instructions; "paired_staged": the same with each direction's words
+ * copied into shared memory by cp.async, FP16 only; "prefetch": one
+ * right-hand side with the loads of several directions issued ahead),
+ * rhs_per_thread, directions_ahead, rhs_groups_per_block (groups run in
+ * sequence by one block), min_blocks_per_sm (register cap),
+ * tiles_per_supertile (block order) and block (threads).  The hopping
+ * kernels time these candidates on their first launch for each (sites,
+ * nrhs, format, mode) and keep the fastest; the environment variables
+ * LQCD_HOP_NR (shape code: 1..3 scalar, 0 paired, -2/-4/-8 prefetch, 12/13
+ * staged 2/3 directions ahead), LQCD_HOP_GPB, LQCD_HOP_MINB and LQCD_HOP_SWZ
+ * force a shape instead.  Returns LQCD_EINVAL
  * if buf is too small (the text is truncated). */
 int lqcd_tune_report(char *buf, size_t len);
 
