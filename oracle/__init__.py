@@ -55,6 +55,11 @@ def _load():
         lib.oracle_cgnr.restype = ctypes.c_int
         lib.oracle_pion_contract.argtypes = [ip, dp, ctypes.c_int, dp]
         lib.oracle_meson_contract.argtypes = [ip, dp, ctypes.c_int, dp, ctypes.c_int, dp]
+        lib.oracle_dirac_tm.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                        ctypes.c_int]
+        lib.oracle_cgnr_tm.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double)]
         lib.oracle_pion.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.c_double, ctypes.c_int, dp, dp, ip, dp]
         lib.oracle_pion.restype = ctypes.c_int
@@ -141,6 +146,26 @@ def cgnr(dims, U, kappa, csw, b, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000,
     res = ctypes.c_double(0)
     st = _load().oracle_cgnr(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, _dp(th),
                              _dp(b), _dp(x), tol, maxiter, ctypes.byref(it), ctypes.byref(res))
+    return x, it.value, res.value, st == 0
+
+
+def dirac_tm(dims, U, kappa, csw, mu, psi, theta=DEFAULT_THETA, dagger=False) -> np.ndarray:
+    """Twisted-mass D(mu) psi = D psi + 2 i kappa mu g5 psi (or its adjoint), FP64."""
+    U, psi, th, d = _c128(U), _c128(psi), _theta(theta), _dims(dims)
+    out = np.zeros_like(psi)
+    _load().oracle_dirac_tm(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, mu,
+                            _dp(th), _dp(psi), _dp(out), int(bool(dagger)))
+    return out
+
+
+def cgnr_tm(dims, U, kappa, csw, mu, b, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000):
+    """Solves D(mu) x = b by CGNR; returns (x, iterations, true relative residual, converged)."""
+    U, b, th, d = _c128(U), _c128(b), _theta(theta), _dims(dims)
+    x = np.zeros_like(b)
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0)
+    st = _load().oracle_cgnr_tm(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, mu, _dp(th),
+                                _dp(b), _dp(x), tol, maxiter, ctypes.byref(it), ctypes.byref(res))
     return x, it.value, res.value, st == 0
 
 

@@ -288,6 +288,7 @@ typedef struct {
     int L[4];
     const double *U;
     double kappa, csw;
+    double mu; /* twisted mass (mass units): site term + 2 i kappa mu g5; 0 for the Wilson-clover D */
     cplx theta[4];
     double *F; /* clover field F[site][plane][3][3], NULL when csw == 0 */
 } dirac_ctx;
@@ -300,6 +301,7 @@ static void ctx_init(dirac_ctx *c, const int *L, const double *U, double kappa, 
     c->U = U;
     c->kappa = kappa;
     c->csw = csw;
+    c->mu = 0.0;
     for (int mu = 0; mu < 4; ++mu) c->theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
     c->F = NULL;
     if (csw != 0.0) {
@@ -352,6 +354,12 @@ static spinor dirac_site(const dirac_ctx *c, const double *psi, long x)
                 }
         }
     }
+    if (c->mu != 0.0) {
+        /* twisted mass, kappa-normalised: + 2 i kappa mu g5 psi(x) */
+        spinor s = spinor_at(psi, x);
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) out.c[al][a] += 2.0 * I * c->kappa * c->mu * G[4][al][al] * s.c[al][a];
+    }
     return out;
 }
 
@@ -391,6 +399,12 @@ static void dirac_dagger_apply(const dirac_ctx *c, const double *in, double *out
                         acc[x].c[al][a] += -I * c->kappa * c->csw * s;
                     }
             }
+        }
+        if (c->mu != 0.0) {
+            /* (2 i kappa mu g5)^dag = -2 i kappa mu g5 */
+            for (int al = 0; al < 4; ++al)
+                for (int a = 0; a < 3; ++a)
+                    acc[x].c[al][a] += -2.0 * I * c->kappa * c->mu * G[4][al][al] * px.c[al][a];
         }
         for (int mu = 0; mu < 4; ++mu) {
             /* term D(x, x+mu) = -kappa (1 - g_mu) U~_mu(x): adjoint goes to x+mu */
@@ -505,11 +519,10 @@ static double norm2(const double *v, long n)
  * restarted from the current x.  Returns 0 on convergence, 1 if maxiter was
  * reached; *iters is the number of D^dag D applications, *resid the last true
  * relative residual. */
-int oracle_cgnr(const int *L, const double *U, double kappa, double csw, const double *theta,
-                const double *b, double *x, double tol, int maxiter, int *iters, double *resid)
+static int cgnr_ctx(dirac_ctx *cp, const int *L, const double *b, double *x, double tol, int maxiter, int *iters,
+                    double *resid)
 {
-    dirac_ctx c;
-    ctx_init(&c, L, U, kappa, csw, theta);
+    dirac_ctx c = *cp;
     long n = 24 * volume_of(L);
     double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
     double *p = malloc(sizeof(double) * n), *w = malloc(sizeof(double) * n);
@@ -520,7 +533,6 @@ int oracle_cgnr(const int *L, const double *U, double kappa, double csw, const d
         memset(x, 0, sizeof(double) * n);
         *iters = 0;
         *resid = 0;
-        ctx_free(&c);
         free(r); free(z); free(p); free(w);
         return 0;
     }
@@ -552,9 +564,47 @@ int oracle_cgnr(const int *L, const double *U, double kappa, double csw, const d
     }
     *iters = it;
     *resid = rel;
-    ctx_free(&c);
     free(r); free(z); free(p); free(w);
     return status;
+}
+
+int oracle_cgnr(const int *L, const double *U, double kappa, double csw, const double *theta,
+                const double *b, double *x, double tol, int maxiter, int *iters, double *resid)
+{
+    dirac_ctx c;
+    ctx_init(&c, L, U, kappa, csw, theta);
+    int st = cgnr_ctx(&c, L, b, x, tol, maxiter, iters, resid);
+    ctx_free(&c);
+    return st;
+}
+
+/* Twisted-mass Wilson-clover operator (DiracParam's mu, Sec. 3.3), read in
+ * the kappa normalisation of oracle_dirac: D(mu) = D + 2 i kappa mu g5, mu in
+ * mass units (the paper's D_w gains + i mu g5, and D = 2 kappa D_w).  The
+ * twist is applied to a single flavour; D(mu)^dag = D^dag - 2 i kappa mu g5. */
+void oracle_dirac_tm(const int *L, const double *U, double kappa, double csw, double mu, const double *theta,
+                     const double *in, double *out, int dagger)
+{
+    dirac_ctx c;
+    ctx_init(&c, L, U, kappa, csw, theta);
+    c.mu = mu;
+    if (dagger)
+        dirac_dagger_apply(&c, in, out);
+    else
+        dirac_apply(&c, in, out);
+    ctx_free(&c);
+}
+
+/* CGNR of oracle_cgnr on D(mu) */
+int oracle_cgnr_tm(const int *L, const double *U, double kappa, double csw, double mu, const double *theta,
+                   const double *b, double *x, double tol, int maxiter, int *iters, double *resid)
+{
+    dirac_ctx c;
+    ctx_init(&c, L, U, kappa, csw, theta);
+    c.mu = mu;
+    int st = cgnr_ctx(&c, L, b, x, tol, maxiter, iters, resid);
+    ctx_free(&c);
+    return st;
 }
 
 /* ------------------------------------------------------------------ */

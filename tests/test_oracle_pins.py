@@ -163,6 +163,72 @@ def test_free_pion_correlator_closed_form():
 
 
 # --------------------------------------------------------------------------
+# twisted mass (DiracParam mu): D(mu) = D + 2 i kappa mu g5
+# --------------------------------------------------------------------------
+
+def test_twisted_mass_free_plane_waves_and_propagator():
+    """Free field: D(mu)(p) = A + 2 i kappa sum g sin p + i M g5 with M = 2 kappa mu,
+    and since g5 anticommutes with every g_mu its inverse is
+    (A - 2 i kappa sum g sin p - i M g5) / (A^2 + 4 kappa^2 sum sin^2 p + M^2)."""
+    dims = (2, 4, 2, 6)
+    kappa, mu = 0.124, 0.35
+    M = 2 * kappa * mu
+    theta = (1, np.exp(0.4j), 1, -1)
+    U = inputs.unit_gauge_field(dims)
+    ps = _momenta(dims, theta)
+    x, y, z, t = _coords(dims)
+    rng = np.random.default_rng(8)
+    for n in [(0, 0, 0, 0), (1, 3, 1, 4)]:
+        p = [ps[m][n[m]] for m in range(4)]
+        phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+        u = rng.normal(size=(4, 3)) + 1j * rng.normal(size=(4, 3))
+        psi = phase[..., None, None] * u
+        want = phase[..., None, None] * ((_free_dirac_p(kappa, p) + 1j * M * G5) @ u)
+        assert rel(oracle.dirac_tm(dims, U, kappa, 1.1, mu, psi, theta=theta), want) < 1e-14
+    # propagator column (spin 2, colour 0) against the momentum sum
+    V = np.prod(dims)
+    P = [a.ravel() for a in np.meshgrid(*ps, indexing="ij")]
+    S = np.zeros(x.shape + (4, 4), dtype=complex)
+    for k in range(len(P[0])):
+        p = [P[m][k] for m in range(4)]
+        A = 1 - 2 * kappa * sum(np.cos(pm) for pm in p)
+        den = A * A + 4 * kappa ** 2 * sum(np.sin(pm) ** 2 for pm in p) + M * M
+        num = A * np.eye(4, dtype=complex) - 1j * M * G5
+        for m in range(4):
+            num = num - 2j * kappa * np.sin(p[m]) * BASIS[m]
+        S += np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))[..., None, None] * (num / den)
+    S /= V
+    eta = inputs.point_source(dims, (0, 0, 0, 0), 2, 0)
+    sol, it, res, ok = oracle.cgnr_tm(dims, U, kappa, 0.0, mu, eta, theta=theta, tol=1e-13)
+    assert ok and res <= 1e-13
+    want = np.zeros_like(sol)
+    want[..., :, 0] = S[..., :, 2]
+    assert rel(sol, want) < 1e-11
+
+
+def test_twisted_mass_identities_on_rough_fields():
+    """With clover on a rough field: mu = 0 is the Wilson-clover D; the
+    adjoint identity; g5 D(mu) g5 = D(-mu)^dag; and, because D = g5 D^dag g5,
+    the cross terms cancel in |D(mu) x|^2 = |D x|^2 + (2 kappa mu)^2 |x|^2."""
+    dims, U = _rough()
+    k, c = ROUGH["kappa"], ROUGH["csw"]
+    mu = 0.27
+    th = (1, np.exp(0.3j), 1, -1)
+    a = inputs.spinor_field(dims, seed=31)
+    b = inputs.spinor_field(dims, seed=32)
+    assert np.array_equal(oracle.dirac_tm(dims, U, k, c, 0.0, a, theta=th), oracle.dirac(dims, U, k, c, a, theta=th))
+    Da = oracle.dirac_tm(dims, U, k, c, mu, a, theta=th)
+    lhs = vdot(b, Da)
+    rhs = vdot(oracle.dirac_tm(dims, U, k, c, mu, b, theta=th, dagger=True), a)
+    assert abs(lhs - rhs) <= 1e-14 * abs(lhs)
+    assert rel(g5(oracle.dirac_tm(dims, U, k, c, mu, g5(a), theta=th)),
+               oracle.dirac_tm(dims, U, k, c, -mu, a, theta=th, dagger=True)) < 1e-14
+    n_mu = np.vdot(Da, Da).real
+    n_0 = np.vdot(*(2 * [oracle.dirac(dims, U, k, c, a, theta=th)])).real
+    assert abs(n_mu - (n_0 + (2 * k * mu) ** 2 * np.vdot(a, a).real)) <= 1e-13 * n_mu
+
+
+# --------------------------------------------------------------------------
 # rough fields: hermiticity, adjoint, covariance
 # --------------------------------------------------------------------------
 
