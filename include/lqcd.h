@@ -81,8 +81,9 @@ typedef struct lqcd_lattice_s *lqcd_lattice; /* opaque; owns all device memory i
 typedef struct lqcd_server_s *lqcd_server;   /* opaque serving loop */
 
 /* DiracParam of Sec. 3.3 (kappa instead of m0).  theta: the four boundary
- * phase factors (|theta_mu| = 1), re and im parts.  mu (twisted mass) must be
- * 0 in this version. */
+ * phase factors (|theta_mu| = 1), re and im parts.  mu (twisted mass, mass
+ * units; the kappa-normalised site term would gain 2 i kappa mu g5) must be
+ * 0 in this version: any call given mu != 0 returns LQCD_ENOTIMPL. */
 typedef struct {
     double kappa;
     double csw;
