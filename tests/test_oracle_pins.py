@@ -451,6 +451,26 @@ def test_meson_gamma5_channel_is_the_pion():
     assert np.max(np.abs(c[0].imag)) < 1e-13 * np.max(p)
 
 
+def test_meson_free_field_symmetries():
+    """Free field on a cubic lattice: every channel is real and symmetric under
+    t -> T - t (time reflection with antiperiodic time), and channels related
+    by a spatial rotation are equal (x, y, z permuted)."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = inputs.unit_gauge_field(dims)
+    _, prop, _, _, failed = oracle.pion(dims, U, kappa, 1.0, (0, 0, 0, 0), tol=1e-13, want_prop=True)
+    assert failed == 0
+    basis = clifford16()
+    c = oracle.meson_contract(dims, prop, 0, basis)
+    scale = np.max(np.abs(c))
+    assert np.max(np.abs(c.imag)) < 1e-14 * scale
+    assert np.max(np.abs(c[:, 1:] - c[:, 1:][:, ::-1])) < 1e-13 * scale
+    # clifford16 order: 1, gx, gy, gz, gt, gxgy, gxgz, gxgt, gygz, gygt, gzgt,
+    # gxgygz, gxgygt, gxgzgt, gygzgt, g5
+    for group in ([1, 2, 3], [5, 6, 8], [7, 9, 10], [12, 13, 14]):
+        for g in group[1:]:
+            assert np.max(np.abs(c[g] - c[group[0]])) < 1e-13 * scale, (group, g)
+
+
 def test_meson_fierz_completeness():
     """Completeness of the Clifford basis, sum_A (G_A)_ab (G_A^dag)_cd =
     4 delta_ad delta_bc, turns the sum over all 16 channels into
