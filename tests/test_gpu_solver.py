@@ -234,3 +234,38 @@ def test_propagator_16x32_full_size(lq, prec):
     for j in (0, 5, 11):
         eta = inputs.point_source(dims, src, j // 3, j % 3)
         assert true_resid(dims, U, kappa, csw, prop[j], eta) <= 1e-10
+
+
+def test_propagator_32x64_bench_configuration(lq):
+    """32^3 x 64, eps 0.4, kappa 0.132, csw 1.7, FP16 storage, 12 RHS, tol
+    1e-10: the benchmark's propagator, in the call the benchmark times.
+
+    Checked at this size: C(t) equals the oracle's contraction of the returned
+    columns, and for three columns the residual eta - D S_j at sampled sites
+    (the source, its 8 neighbours, two corners and 300 random sites), with
+    the oracle's D, is at most 1e-10 per site: |eta| = 1, so a true residual
+    <= 1e-10 bounds every site.
+    """
+    dims, kappa, csw = (32, 32, 32, 64), 0.132, 1.7
+    U = inputs.gauge_field(dims, 0.4, seed=1, workers=None)
+    src = (0, 0, 0, 0)
+    lat = lq.lattice_create(dims)
+    try:
+        gid = lq.gauge_upload(lat, U)
+        corr, prop, info, rc = lq.pion_corr(lat, gid, lq.dirac_params(kappa, csw),
+                                            lq.solver_params(tol=1e-10, maxiter=20000, precision="fp16"), src,
+                                            dims=dims, want_prop=True)
+    finally:
+        lq.lattice_destroy(lat)
+    assert rc == lq.OK, info
+    assert max(i["true_resid"] for i in info) <= 1e-10
+    assert np.allclose(corr, oracle.pion_contract(dims, prop, src[3]), rtol=1e-12, atol=0)
+    V = inputs.volume(dims)
+    # source at the origin; lexicographic index x + 32 (y + 32 (z + 32 t))
+    near = [0, 1, 31, 32, 32 * 31, 32 * 32, 32 * 32 * 31, 32 ** 3, 32 ** 3 * 63, V - 1]
+    rng = np.random.default_rng(1)
+    sites = np.unique(np.concatenate([near, rng.integers(0, V, 300)]))
+    for j in (0, 5, 11):
+        eta = inputs.point_source(dims, src, j // 3, j % 3).reshape(V, 4, 3)[sites]
+        r = eta - oracle.dirac_sites(dims, U, kappa, csw, prop[j], sites)
+        assert np.max(np.abs(r)) <= 1e-10, (j, np.max(np.abs(r)))
