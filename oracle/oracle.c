@@ -466,6 +466,7 @@ void oracle_dirac_sites(const int *L, const double *U, double kappa, double csw,
     c.U = U;
     c.kappa = kappa;
     c.csw = csw;
+    c.mu = 0.0; /* the Wilson-clover D: no twisted-mass term */
     for (int mu = 0; mu < 4; ++mu) c.theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
     double Fx[108];
     for (long k = 0; k < nsites; ++k) {

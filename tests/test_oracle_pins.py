@@ -536,3 +536,34 @@ def test_gauge_generator_su3_and_mean_plaquette():
     assert abs(plaq - u ** 4) < 0.01
     # second-order expansion of the mean link: u = 1 - 2 eps^2 / 3 + O(eps^4)
     assert abs(u - (1 - 2 * eps ** 2 / 3)) < 0.02
+
+
+# --------------------------------------------------------------------------
+# the per-site operator used on lattices too large for a full application
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,eps,kappa,csw,theta", [
+    ((4, 4, 4, 4), 0.5, 0.13, 1.7, (np.exp(0.4j), np.exp(-1.3j), np.exp(2.1j), -np.exp(0.6j))),
+    ((4, 6, 2, 10), 0.6, 0.125, 1.5, (np.exp(-0.8j), 1, np.exp(1.7j), -1)),
+    ((2, 2, 4, 2), 0.4, 0.14, 2.0, (1, np.exp(0.9j), 1, np.exp(-2.5j))),
+    ((6, 4, 4, 8), 0.4, 0.132, 0.0, (1, 1, 1, -1)),
+])
+def test_dirac_sites_equals_full_operator(dims, eps, kappa, csw, theta):
+    """oracle.dirac_sites rebuilds the clover term per site; at every site of
+    rough fields with twisted phases in all four directions, extents of 2 and
+    ragged extents it must equal the full-lattice operator, and
+    g5 D(g5 psi) at the sites must equal the full D^dag (the use the parity
+    tests make of it for the adjoint)."""
+    U = inputs.gauge_field(dims, eps, seed=21)
+    psi = inputs.spinor_field(dims, seed=22)
+    V = int(np.prod(dims))
+    sites = np.arange(V)
+    full = oracle.dirac(dims, U, kappa, csw, psi, theta=theta).reshape(V, 4, 3)
+    got = oracle.dirac_sites(dims, U, kappa, csw, psi, sites, theta=theta)
+    assert np.max(np.abs(got - full)) <= 1e-14 * np.max(np.abs(full))
+    # a shuffled subset returns the same rows in the requested order
+    pick = np.random.default_rng(3).permutation(V)[: V // 3]
+    assert np.array_equal(oracle.dirac_sites(dims, U, kappa, csw, psi, pick, theta=theta), got[pick])
+    dag = oracle.dirac(dims, U, kappa, csw, psi, theta=theta, dagger=True).reshape(V, 4, 3)
+    g5d = np.einsum("ab,kbc->kac", G5, oracle.dirac_sites(dims, U, kappa, csw, g5(psi), sites, theta=theta))
+    assert np.max(np.abs(g5d - dag)) <= 1e-14 * np.max(np.abs(dag))
