@@ -71,10 +71,11 @@ enum {
                                  clover, FP32 math; FP64 outer */
 };
 
-/* flags for lqcd_dirac_apply / lqcd_pion_contract */
+/* flags for lqcd_dirac_apply / lqcd_pion_contract / lqcd_cg_solve */
 enum {
     LQCD_DAG = 1,         /* apply D^dag = g5 D g5 instead of D */
-    LQCD_DEVICE_PTRS = 2  /* psi_in / psi_out (or prop / corr) are device pointers */
+    LQCD_DEVICE_PTRS = 2, /* psi_in / psi_out (or prop / corr, b / x) are device pointers */
+    LQCD_GUESS = 4        /* lqcd_cg_solve: x holds an initial guess on input (resume, warm start) */
 };
 
 typedef struct lqcd_lattice_s *lqcd_lattice; /* opaque; owns all device memory it allocates */
@@ -182,9 +183,15 @@ int lqcd_schur_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp
  * (A = clover site term, H = hopping term), with FP64 residual recomputation
  * (reliable updates) and an FP64 final true-residual check on the full
  * lattice.  b, x: nrhs * 24 V doubles, host layout; host memory, or device
- * memory when flags has LQCD_DEVICE_PTRS.  x on input is ignored (zero start).
- * info: nrhs entries (may be NULL).  sp->nrhs is ignored; nrhs is the
- * argument.
+ * memory when flags has LQCD_DEVICE_PTRS.  x on input: with LQCD_GUESS in
+ * flags, the initial guess x_0 (the CG! of Sec. 3.3 works on a given field:
+ * a solve resumed from a saved x_0, or warm-started from a nearby solution);
+ * the first FP64 residual is b - D x_0, so a guess that already meets tol
+ * returns after that check with iters_inner = 0.  Only the even-site part of
+ * x_0 enters (the odd part is rebuilt from it, x_o = A_oo^-1 (b_o +
+ * kappa H_oe x_e)).  Without LQCD_GUESS, x on input is ignored (zero start).
+ * x may not overlap b.  info: nrhs entries (may be NULL).  sp->nrhs is
+ * ignored; nrhs is the argument.
  * Returns LQCD_OK when every column reached sp->tol, LQCD_ENOCONV when one
  * did not (x and info still filled), or an error. */
 int lqcd_cg_solve(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
@@ -361,8 +368,11 @@ int lqcd_serve_submit(lqcd_server srv, int gauge_id, const lqcd_dirac_params *dp
 int lqcd_serve_poll(lqcd_server srv, uint64_t ticket, double *corr, lqcd_solve_info *info,
                     double timestamps[4], int timeout_ms);
 
-/* Stops the device thread; requests not finished yet are cancelled and
- * their tickets forgotten.  Frees everything.  NULL is accepted. */
+/* Stops the device threads: queued requests finish at once and running ones
+ * at their next poll, all with LQCD_ETIMEOUT ("server stopped"), so a
+ * lqcd_serve_poll already waiting returns; destroy waits for such polls to
+ * leave, then frees everything.  No call on srv may start once destroy has
+ * begun.  NULL is accepted. */
 int lqcd_serve_destroy(lqcd_server srv);
 
 #ifdef __cplusplus

@@ -229,10 +229,11 @@ int lqcd_cg_solve(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, c
         lat->staging.ensure(bytes);
         lat->staging2.ensure(bytes);
         LQCD_CUDA(cudaMemcpyAsync(lat->staging.p, b, bytes, cudaMemcpyHostToDevice, st));
+        if (flags & LQCD_GUESS) LQCD_CUDA(cudaMemcpyAsync(lat->staging2.p, x, bytes, cudaMemcpyHostToDevice, st));
         bd = lat->staging.as<const double>();
         xd = lat->staging2.as<double>();
     }
-    int failed = solve(lat, gauge_id, *dp, *sp, bd, xd, nullptr, nrhs, info, nullptr, st);
+    int failed = solve(lat, gauge_id, *dp, *sp, bd, xd, nullptr, nrhs, info, nullptr, st, (flags & LQCD_GUESS) != 0);
     if (!(flags & LQCD_DEVICE_PTRS)) {
         LQCD_CUDA(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, st));
         LQCD_CUDA(cudaStreamSynchronize(st));

@@ -14,45 +14,66 @@ __global__ void __launch_bounds__(128) norm2_f64(VecArgs v, SpinorField<F64> x)
     reduce_finish(v.red, j, tile, v.ntiles, n2);
 }
 
+// Partial of 128-site tile k of RHS j.  QUAD: the FP32 sums of its four
+// 32-site quarters, combined as the 128-thread block of reduce_partial2
+// combines its four warps ((q0 + q2) + (q1 + q3), in FP32), so both give the
+// same value.
+template <bool QUAD>
+__device__ __forceinline__ double tile_partial(const Reduce &r, int j, int ntiles, int k)
+{
+    if constexpr (QUAD) {
+        const float *q = r.partial_f + ((long)j * ntiles + k) * 4;
+        return double((q[0] + q[2]) + (q[1] + q[3]));
+    } else {
+        return r.partial[(long)j * ntiles + k];
+    }
+}
+
 // Sum of the per-tile partials of each gated-in RHS (one block of 512
 // threads per RHS, four independent accumulators per thread, fixed order:
 // deterministic) and its operation.
 constexpr int kFinishThreads = 512;
+template <bool QUAD>
 __global__ void __launch_bounds__(kFinishThreads) partial_finish_kernel(Reduce r, int ntiles, const RhsState *gate_st,
                                                                        int gate)
 {
     __shared__ double sh[32];
     const int j = blockIdx.x;
     if (gate_st && gate_st[j].status != gate) return;
-    const double *p = r.partial + (long)j * ntiles;
     double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
     int k = threadIdx.x;
     for (; k + 3 * kFinishThreads < ntiles; k += 4 * kFinishThreads) {
-        t0 += p[k];
-        t1 += p[k + kFinishThreads];
-        t2 += p[k + 2 * kFinishThreads];
-        t3 += p[k + 3 * kFinishThreads];
+        t0 += tile_partial<QUAD>(r, j, ntiles, k);
+        t1 += tile_partial<QUAD>(r, j, ntiles, k + kFinishThreads);
+        t2 += tile_partial<QUAD>(r, j, ntiles, k + 2 * kFinishThreads);
+        t3 += tile_partial<QUAD>(r, j, ntiles, k + 3 * kFinishThreads);
     }
-    for (; k < ntiles; k += kFinishThreads) t0 += p[k];
+    for (; k < ntiles; k += kFinishThreads) t0 += tile_partial<QUAD>(r, j, ntiles, k);
     double t = block_sum((t0 + t1) + (t2 + t3), sh);
     if (threadIdx.x == 0) apply_op(r, j, t);
 }
 
-void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st)
+void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st,
+                           bool quad)
 {
-    ProfScope prof("norm_finish", double(nrhs) * ntiles * 8.0, st);
-    partial_finish_kernel<<<unsigned(nrhs), kFinishThreads, 0, st>>>(r, ntiles, gate_st, gate);
+    ProfScope prof("norm_finish", double(nrhs) * ntiles * (quad ? 16.0 : 8.0), st);
+    if (quad)
+        partial_finish_kernel<true><<<unsigned(nrhs), kFinishThreads, 0, st>>>(r, ntiles, gate_st, gate);
+    else
+        partial_finish_kernel<false><<<unsigned(nrhs), kFinishThreads, 0, st>>>(r, ntiles, gate_st, gate);
     LQCD_CHECK_LAUNCH();
 }
 
 static unsigned grid_of(const VecArgs &v) { return unsigned(v.ntiles * v.nrhs); }
+// right-hand sides a launch is expected to work on (accounting only)
+static double nact(const VecArgs &v) { return v.nactive >= 0 ? std::min(v.nactive, v.nrhs) : v.nrhs; }
 
 template <class W, class E>
 void launch_er_update(const VecArgs &v, SpinorField<W> p, SpinorField<W> w, SpinorField<W> r, SpinorField<E> e,
                       cudaStream_t st)
 {
     ProfScope prof(prec_name<W>() == std::string("f64") ? "cg_er_update_f64" : (prec_name<W>() == std::string("f32") ? "cg_er_update_f32" : "cg_er_update_f16"),
-                   double(v.vh) * v.nrhs * (4.0 * spinor_bytes<W>() + 2.0 * spinor_bytes<E>()), st);
+                   double(v.vh) * nact(v) * (4.0 * spinor_bytes<W>() + 2.0 * spinor_bytes<E>()), st);
     cg_er_update<W, E><<<grid_of(v), kBlock, 0, st>>>(v, p, w, r, e);
     LQCD_CHECK_LAUNCH();
 }
@@ -60,7 +81,7 @@ void launch_er_update(const VecArgs &v, SpinorField<W> p, SpinorField<W> w, Spin
 template <class W>
 void launch_p_update(const VecArgs &v, const RhsState *s, SpinorField<W> z, SpinorField<W> p, cudaStream_t st)
 {
-    ProfScope prof("cg_p_update", double(v.vh) * v.nrhs * 3.0 * spinor_bytes<W>(), st);
+    ProfScope prof("cg_p_update", double(v.vh) * nact(v) * 3.0 * spinor_bytes<W>(), st);
     cg_p_update<W><<<grid_of(v), kBlock, 0, st>>>(v, s, z, p);
     LQCD_CHECK_LAUNCH();
 }
@@ -68,7 +89,7 @@ void launch_p_update(const VecArgs &v, const RhsState *s, SpinorField<W> z, Spin
 template <class E>
 void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, SpinorField<F64> x, cudaStream_t st)
 {
-    ProfScope prof("cg_x_update", double(v.vh) * v.nrhs * (2.0 * spinor_bytes<E>() + 2.0 * 192.0), st);
+    ProfScope prof("cg_x_update", double(v.vh) * nact(v) * (2.0 * spinor_bytes<E>() + 2.0 * 192.0), st);
     cg_x_update<E><<<grid_of(v), kBlock, 0, st>>>(v, s, e, x);
     LQCD_CHECK_LAUNCH();
 }
@@ -76,7 +97,7 @@ void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, Spin
 template <class W>
 void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> w, SpinorField<W> r, cudaStream_t st)
 {
-    ProfScope prof("cg_r_replace", double(v.vh) * v.nrhs * (2.0 * 192.0 + spinor_bytes<W>()), st);
+    ProfScope prof("cg_r_replace", double(v.vh) * nact(v) * (2.0 * 192.0 + spinor_bytes<W>()), st);
     cg_r_replace<W><<<grid_of(v), kBlock, 0, st>>>(v, bhat, w, r);
     LQCD_CHECK_LAUNCH();
 }

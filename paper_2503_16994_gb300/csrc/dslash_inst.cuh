@@ -4,6 +4,7 @@
 #include <cstdlib>
 
 #include "hopfast.cuh"
+#include "hopt.cuh"
 #include "lqcd_impl.h"
 
 namespace lqcd {
@@ -46,6 +47,9 @@ template <class S>
 void hopp_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st);
 // staged paired kernel (hops_f16.cu): pd directions of cp.async copies ahead
 void hops_dispatch(const FastHop<F16> &f, int pd, int mode, bool dag, bool norm, cudaStream_t st);
+// tile kernel (hopt_f16.cu): links, clover and neighbours prepared once per
+// 32-site tile in shared memory; pf: one direction of loads ahead
+void hopt_dispatch(const FastHop<F16> &f, bool pf, int mode, bool dag, bool norm, cudaStream_t st);
 
 template <class S, int MODE, bool DAG, bool NORM>
 static void hopq_go(const FastHop<S> &f, int pf, cudaStream_t st)
@@ -73,11 +77,19 @@ static void hopq_dispatch(const FastHop<S> &f, int pf, int mode, bool dag, bool 
 // nr == -2, -4, -8: one right-hand side per thread, loads of 2, 4 or 8
 // directions issued before their arithmetic (FP16/FP32 only);
 // nr == 12, 13: as nr == 0 with the words of 2 or 3 directions ahead staged
-// in shared memory by cp.async (FP16 only)
+// in shared memory by cp.async (FP16 only);
+// nr == 20, 21: the tile kernel, gpb = pairs (warps) per block, 21 with one
+// direction of loads ahead (FP16 only)
+constexpr bool is_tile_shape(int nr) { return nr == 20 || nr == 21; }
+
 template <class S>
 static void hopf_launch(const FastHop<S> &f, int nr, int mode, bool dag, bool norm, cudaStream_t st)
 {
     if constexpr (std::is_same<S, F16>::value) {
+        if (is_tile_shape(nr)) {
+            hopt_dispatch(f, nr == 21, mode, dag, norm, st);
+            return;
+        }
         if (nr >= 12) {
             hops_dispatch(f, nr - 10, mode, dag, norm, st);
             return;
@@ -122,9 +134,10 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
     const char *env_gpb = std::getenv("LQCD_HOP_GPB");
     if (env_nr || env_gpb) {
         int nr = env_nr ? std::atoi(env_nr) : 1, gpb = env_gpb ? std::atoi(env_gpb) : 1;
-        const bool staged = std::is_same<S, F16>::value && (nr == 12 || nr == 13);
+        const bool staged = std::is_same<S, F16>::value && (nr == 12 || nr == 13 || is_tile_shape(nr));
         if (std::is_same<S, F64>::value || (!staged && nr != -2 && nr != -4 && nr != -8 && (nr < 0 || nr > 3)))
             nr = 1;
+        if (is_tile_shape(nr) && !env_gpb) gpb = std::min(kTileMaxPairs, (f.nrhs + 1) / 2);
         const char *env_mb = std::getenv("LQCD_HOP_MINB");
         const char *env_sw = std::getenv("LQCD_HOP_SWZ");
         return HopShape{nr, std::max(gpb, 1), env_mb ? std::atoi(env_mb) : 1, env_sw ? std::max(1, std::atoi(env_sw)) : 1};
@@ -175,6 +188,14 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
                 cand.push_back(HopShape{12, gpb, 4, 1});
                 cand.push_back(HopShape{13, gpb, 3, 1});
             }
+        // tile kernel: all pairs of a tile in one block (up to 6 warps), or half of them
+        if (ngr >= 3) {
+            const int full = std::min(ngr, kTileMaxPairs);
+            for (int npw : {full, (full % 2 == 0 && full >= 4) ? full / 2 : 0})
+                if (npw > 0)
+                    for (int nr : {20, 21})
+                        for (int minb : {2, 3}) cand.push_back(HopShape{nr, npw, minb, 1});
+        }
     }
     if (!std::is_same<S, F64>::value)
         for (int pf : {2, 4, 8})
@@ -282,6 +303,7 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
     // algorithmic bytes: input spinor (read once), output, self / b where used,
     // 8 links per output site, the clover blocks where used
     const double sb = spinor_bytes<S>();
+    const int nact = a.nactive >= 0 ? std::min(a.nactive, a.nrhs) : a.nrhs;  // RHS that pass the gate
     double per_rhs = sb + (mode == RESID ? 0.0 : sb) + (mode == HOP_CLOV ? 0.0 : sb) + (mode == RESID ? sb : 0.0);
     double shared = 8.0 * link_bytes<L>() + (mode == SELF_PLAIN ? 0.0 : clover_bytes<C>());
     const int pi = S::W == 2 ? 0 : (S::W == 4 ? 1 : 2);
@@ -291,15 +313,17 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
         f.gpb = sh.gpb;
         f.minb = sh.minb;
         f.swz = sh.swz;
+        const bool quad = is_tile_shape(sh.nr);
+        if (quad && norm && !a.red.partial_f) throw Error{LQCD_EINVAL, "tile hopping kernel: no FP32 partials"};
         {
-            ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
+            ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (nact * per_rhs + (nact ? shared : 0.0)), st);
             hopf_launch<S>(f, sh.nr, mode, dag, norm, st);
             LQCD_CHECK_LAUNCH();
         }
-        if (norm) launch_partial_finish(a.red, a.ntiles, a.nrhs, a.gate_st, a.gate, st);
+        if (norm) launch_partial_finish(a.red, a.ntiles, a.nrhs, a.gate_st, a.gate, st, quad);
         return;
     }
-    ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (a.nrhs * per_rhs + shared), st);
+    ProfScope prof(kHopNames[pi][mode], double(a.g.vh) * (nact * per_rhs + (nact ? shared : 0.0)), st);
     bool ok = hop_mode<S, L, C, HOP_CLOV>(a, mode, dag, norm, st) || hop_mode<S, L, C, SELF_CLOV>(a, mode, dag, norm, st);
     if constexpr (std::is_same<S, F64>::value) {
         ok = ok || hop_mode<S, L, C, SELF_PLAIN>(a, mode, dag, norm, st) ||

@@ -46,6 +46,7 @@ struct Reduce {
     unsigned *counter;   // [nrhs], zero between uses
     RhsState *st;        // [nrhs]
     int op;
+    float *partial_f;    // [nrhs][4 ntiles]: FP32 sums per 32 sites (tile hopping kernel), or null
 };
 
 __device__ __forceinline__ void apply_op(const Reduce &r, int j, double sum)
@@ -191,6 +192,7 @@ struct HopArgs {
     const RhsState *gate_st;  // nullptr: every RHS runs
     int gate;                 // RHS j runs only if gate_st[j].status == gate
     Reduce red;
+    int nactive = -1;         // launch accounting only: right-hand sides expected to pass the gate (-1: all)
 };
 
 template <class S, class L, class C, typename R, int MU, int SGN>
@@ -294,6 +296,7 @@ struct VecArgs {
     const RhsState *gate_st;
     int gate;
     Reduce red;
+    int nactive = -1;  // launch accounting only: right-hand sides expected to pass the gate (-1: all)
 };
 
 // e += alpha p ; r -= alpha w ; |r|^2 -> RED_RUPDATE

@@ -210,7 +210,9 @@ void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> 
                       cudaStream_t st);
 void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st);
 // finishes the per-tile partials a hopping kernel wrote with reduce_partial
-void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st);
+// (quad: the FP32 32-site partials of the tile kernel in r.partial_f)
+void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st,
+                           bool quad = false);
 template <class S, class C>
 void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
                          cudaStream_t st);
@@ -223,9 +225,11 @@ void schur_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
                      double *out, int nrhs, int repeat, bool dag, cudaStream_t st);
 void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
                      bool dag, cudaStream_t st);
+// guess: x_dev holds an initial guess on entry (host layout, device memory);
+// otherwise the solve starts from zero
 int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,
           const double *b_dev, double *x_dev, const int *src, int nrhs, lqcd_solve_info *info, double *corr_dev,
-          cudaStream_t st);
+          cudaStream_t st, bool guess = false);
 // Batched propagators over uneven lattices (lqcd_pion_corr_batch); returns
 // the number of jobs with a column that did not converge.
 int pion_batch(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int chunk, cudaStream_t origin);
@@ -234,6 +238,7 @@ int pion_batch(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int chu
 // early when *cancel becomes true (then returns nrhs).
 int solve_on(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,
              const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
-             lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel);
+             lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel,
+             bool guess = false);
 
 }  // namespace lqcd

@@ -47,11 +47,13 @@ Workspace::~Workspace()
     }
 }
 
-// partial sums: the solver's reductions need nrhs * ntiles, the contraction
-// T * ceil(V3/2 / 128) <= ntiles + T; counters: max(nrhs, T)
+// partial sums: the solver's reductions need nrhs * ntiles doubles followed
+// by the 4 nrhs ntiles FP32 partials of the tile hopping kernel (the room of
+// 2 nrhs ntiles doubles), the contraction T * ceil(V3/2 / 128) <= ntiles + T;
+// counters: max(nrhs, T)
 static size_t partial_count(const lqcd_lattice_s *lat, int nrhs)
 {
-    return std::max((size_t)nrhs * ntiles_of(lat->vh), (size_t)ntiles_of(lat->vh) + lat->dims[3]);
+    return std::max(3 * (size_t)nrhs * ntiles_of(lat->vh), (size_t)ntiles_of(lat->vh) + lat->dims[3]);
 }
 
 template <class W, class E>
@@ -200,7 +202,8 @@ struct Solver {
         aw = clover_field<W>(cl, false, Sd);
         aiw = clover_field<W>(cl, true, Sd);
         const int nt = ntiles_of(lat->vh);
-        Reduce red{ws.partial.as<double>(), ws.counter.as<unsigned>(), S, RED_STORE};
+        Reduce red{ws.partial.as<double>(), ws.counter.as<unsigned>(), S, RED_STORE,
+                   reinterpret_cast<float *>(ws.partial.as<double>() + (size_t)nrhs * nt)};
         v = VecArgs{int(lat->vh), nrhs, nt, nullptr, 0, red};
         h64 = HopArgs<F64, F64, F64>{};
         h64.g = lat->geom;
@@ -224,19 +227,26 @@ struct Solver {
         hw.red = red;
     }
 
+    // right-hand sides expected to pass each gate, from the last host poll
+    // (launch accounting only; -1 when unknown)
+    int hint_active = -1, hint_update = -1;
+    int hint(int gate) const { return gate == ST_UPDATE ? hint_update : hint_active; }
+
     VecArgs gated(int gate, int op) const
     {
         VecArgs q = v;
         q.gate_st = S;
         q.gate = gate;
         q.red.op = op;
+        q.nactive = hint(gate);
         return q;
     }
 
     // |b|^2, bhat = b_e + k H_eo A_oo^-1 b_o, state initialisation, x = e = p = 0
     int resume = ST_ACTIVE;  // ST_RESUME for batched solves (the update happens between graph chunks)
 
-    void prepare(double tol_eff, double delta, int maxiter)
+    // guess: x_e already holds the even part of an initial guess (kept)
+    void prepare(double tol_eff, double delta, int maxiter, bool guess)
     {
         VecArgs q = v;
         q.red.op = RED_STORE;
@@ -254,7 +264,7 @@ struct Solver {
         init_state_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(S, nrhs, tol_eff * tol_eff, delta * delta, maxiter,
                                                            resume);
         LQCD_CHECK_LAUNCH();
-        LQCD_CUDA(cudaMemsetAsync(ws.x_e.p, 0, ws.x_e.bytes, st));
+        if (!guess) LQCD_CUDA(cudaMemsetAsync(ws.x_e.p, 0, ws.x_e.bytes, st));
         LQCD_CUDA(cudaMemsetAsync(ws.e.p, 0, ws.e.bytes, st));
         LQCD_CUDA(cudaMemsetAsync(ws.p.p, 0, ws.p.bytes, st));
         if (ws.p_sc.p) LQCD_CUDA(cudaMemsetAsync(ws.p_sc.p, 0, ws.p_sc.bytes, st));
@@ -267,6 +277,7 @@ struct Solver {
         HopArgs<F64, F64, F64> a = h64;
         a.gate_st = S;
         a.gate = ST_UPDATE;
+        a.nactive = hint_update;
         a.parity = 1;
         a.in = x_e;
         a.out = t64;
@@ -289,6 +300,7 @@ struct Solver {
         HopArgs<W, W, W> a = hw;
         a.gate_st = S;
         a.gate = ST_ACTIVE;
+        a.nactive = hint_active;
         a.parity = 1;
         a.in = p;
         a.out = t;
@@ -312,6 +324,7 @@ struct Solver {
         HopArgs<W, W, W> a = hw;
         a.gate_st = S;
         a.gate = gate;
+        a.nactive = hint(gate);
         a.parity = 1;
         a.in = r;
         a.out = t;
@@ -393,6 +406,14 @@ struct Solver {
     {
         LQCD_CUDA(cudaMemcpyAsync(ws.host_state, S, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, st));
         LQCD_CUDA(cudaStreamSynchronize(st));
+        // an RHS updated in FP64 next resumes the inner iteration (or is done)
+        int act = 0, upd = 0;
+        for (int j = 0; j < nrhs; ++j) {
+            act += ws.host_state[j].status == ST_ACTIVE || ws.host_state[j].status == ST_UPDATE;
+            upd += ws.host_state[j].status == ST_UPDATE;
+        }
+        hint_active = act;
+        hint_update = upd;
     }
 
     void push_states()
@@ -420,8 +441,9 @@ struct Solver {
 
     double tol_ = 0, delta_ = 0;
 
-    // |b|, bhat, the FP64 residual of the zero start and the first z, p
-    void start(const lqcd_solver_params &sp)
+    // |b|, bhat, the FP64 residual of the start (zero, or the guess already
+    // in x_e) and the first z, p
+    void start(const lqcd_solver_params &sp, bool guess = false)
     {
         // default reliable-update factor per inner format (measured at
         // 32^3 x 64): FP16 residuals drift, so they are refreshed every
@@ -429,7 +451,7 @@ struct Solver {
         const double delta_default = std::is_same<W, F16>::value ? 0.1 : 0.005;
         delta_ = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : delta_default);
         tol_ = sp.tol;
-        prepare(0.5 * tol_, delta_, sp.maxiter);
+        prepare(0.5 * tol_, delta_, sp.maxiter, guess);
         reliable_update();
         half2();
     }
@@ -447,6 +469,7 @@ struct Solver {
         long guard = (long)sp.maxiter + 64;
         bool finished = false;
         for (long it = 0; it < guard && !finished && !(cancel && *cancel); it += chunk) {
+            if (!poll_each) hint_active = hint_update = -1;  // statuses change unseen inside a chunk
             for (int k = 0; k < chunk; ++k) {
                 half1();
                 if (poll_each) {
@@ -510,9 +533,9 @@ struct Solver {
     }
 
     // returns the number of RHS that did not reach tol
-    int run(const lqcd_solver_params &sp, lqcd_solve_info *info)
+    int run(const lqcd_solver_params &sp, lqcd_solve_info *info, bool guess)
     {
-        start(sp);
+        start(sp, guess);
         iterate(sp);
         return finish_report(sp, info);
     }
@@ -521,7 +544,8 @@ struct Solver {
 template <class W, class E>
 static int solve_on_t(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,
                       const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
-                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel)
+                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel,
+                      bool guess)
 {
     Solver<W, E> s(lat, ws, g, cl, dp, nrhs, st);
     s.cancel = cancel;
@@ -529,7 +553,9 @@ static int solve_on_t(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace
         point_sources(lat, src, s.b_e, s.b_o, st);
     else
         spinor_to_soa(lat, b_dev, nrhs, s.b_e, s.b_o, st);
-    int failed = s.run(sp, info);
+    guess = guess && x_dev;
+    if (guess) spinor_to_soa(lat, x_dev, nrhs, s.x_e, s.x_o, st);  // only the even part is used
+    int failed = s.run(sp, info, guess);
     if (cancel && *cancel) failed = nrhs;
     if (x_dev) spinor_from_soa(lat, x_dev, nrhs, s.x_e, s.x_o, st);
     if (corr_dev)
@@ -540,15 +566,18 @@ static int solve_on_t(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace
 
 int solve_on(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, const lqcd_dirac_params &dp,
              const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
-             lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel)
+             lqcd_solve_info *info, double *corr_dev, cudaStream_t st, const volatile bool *cancel, bool guess)
 {
     switch (sp.precision) {
     case LQCD_PREC_FP64:
-        return solve_on_t<F64, F64>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel);
+        return solve_on_t<F64, F64>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel,
+                                    guess);
     case LQCD_PREC_MIXED_FP32:
-        return solve_on_t<F32, F32>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel);
+        return solve_on_t<F32, F32>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel,
+                                    guess);
     case LQCD_PREC_MIXED_FP16:
-        return solve_on_t<F16, F32>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel);
+        return solve_on_t<F16, F32>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, cancel,
+                                    guess);
     default: throw Error{LQCD_EINVAL, "unknown precision"};
     }
 }
@@ -556,10 +585,10 @@ int solve_on(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, Workspace &ws, con
 template <class W, class E>
 static int solve_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, const lqcd_dirac_params &dp,
                       const lqcd_solver_params &sp, const double *b_dev, double *x_dev, const int *src, int nrhs,
-                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st)
+                      lqcd_solve_info *info, double *corr_dev, cudaStream_t st, bool guess)
 {
     Workspace &ws = workspace<W, E>(lat, nrhs, sp.precision, st);
-    return solve_on_t<W, E>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, nullptr);
+    return solve_on_t<W, E>(lat, g, cl, ws, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, nullptr, guess);
 }
 
 void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
@@ -628,18 +657,19 @@ void schur_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
 
 int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const lqcd_solver_params &sp,
           const double *b_dev, double *x_dev, const int *src, int nrhs, lqcd_solve_info *info, double *corr_dev,
-          cudaStream_t st)
+          cudaStream_t st, bool guess)
 {
     auto it = lat->gauges.find(gauge_id);
     if (it == lat->gauges.end()) throw Error{LQCD_EINVAL, "unknown gauge id"};
     GaugeSet &g = *it->second;
     CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
     switch (sp.precision) {
-    case LQCD_PREC_FP64: return solve_prec<F64, F64>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+    case LQCD_PREC_FP64:
+        return solve_prec<F64, F64>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, guess);
     case LQCD_PREC_MIXED_FP32:
-        return solve_prec<F32, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+        return solve_prec<F32, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, guess);
     case LQCD_PREC_MIXED_FP16:
-        return solve_prec<F16, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st);
+        return solve_prec<F16, F32>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, guess);
     default: throw Error{LQCD_EINVAL, "unknown precision"};
     }
 }
@@ -718,6 +748,7 @@ static int batch_t(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int
         LQCD_CUDA(cudaEventRecord(fork, origin));
         for (auto &b : J) {
             if (!b->active) continue;
+            b->s->hint_active = b->s->hint_update = -1;  // the graph is replayed as statuses change
             LQCD_CUDA(cudaStreamWaitEvent(b->st, fork, 0));
             for (int k = 0; k < chunk; ++k) {
                 b->s->half1();

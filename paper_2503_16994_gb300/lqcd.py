@@ -21,7 +21,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBUSY, ETIMEOUT, ENOTFOUND, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6, -7, -8
 PREC_FP64, PREC_MIXED_FP32, PREC_MIXED_FP16 = 0, 1, 2
-DAG, DEVICE_PTRS = 1, 2
+DAG, DEVICE_PTRS, GUESS = 1, 2, 4
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_MIXED_FP32, "fp16": PREC_MIXED_FP16}
 STATUS_NAMES = {0: "LQCD_OK", -1: "LQCD_EINVAL", -2: "LQCD_ENOMEM", -3: "LQCD_ECUDA", -4: "LQCD_ENOCONV",
                 -5: "LQCD_EBUSY", -6: "LQCD_ETIMEOUT", -7: "LQCD_ENOTFOUND", -8: "LQCD_ENOTIMPL"}
@@ -249,21 +249,32 @@ def schur_apply(lat, gauge_id, params: DiracParams, psi, precision="fp64", nrhs=
     return o
 
 
-def cg_solve(lat, gauge_id, params: DiracParams, solver: SolverParams, b, nrhs=1, x=None, stream=None):
-    """Solves D x_j = b_j.  Returns (x, [info dicts], status)."""
+def cg_solve(lat, gauge_id, params: DiracParams, solver: SolverParams, b, nrhs=1, x=None, stream=None,
+             guess=False):
+    """Solves D x_j = b_j.  Returns (x, [info dicts], status).
+
+    ``guess=True``: ``x`` (required then) holds the initial guess and receives
+    the solution (``LQCD_GUESS``); otherwise the solve starts from zero."""
     info = (SolveInfo * nrhs)()
+    if guess and x is None:
+        raise ValueError("guess=True needs x (the initial guess)")
+    flags = GUESS if guess else 0
     if _is_cuda_tensor(b):
         if x is None:
             x = b.new_empty(b.shape)
         n = b.numel() * (2 if b.is_complex() else 1)
         rc = load().lqcd_cg_solve(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver), _dev_ptr(b, n),
-                                  _dev_ptr(x, n), int(nrhs), info, DEVICE_PTRS, _stream_of(b, stream))
+                                  _dev_ptr(x, n), int(nrhs), info, DEVICE_PTRS | flags, _stream_of(b, stream))
     else:
         bb = _host(b)
-        x = np.empty_like(bb) if x is None else x
+        if x is None:
+            x = np.empty_like(bb)
+        elif not (isinstance(x, np.ndarray) and x.dtype == bb.dtype and x.shape == bb.shape
+                  and x.flags.c_contiguous):
+            raise ValueError("x must be a C-contiguous array of b's dtype and shape")
         rc = load().lqcd_cg_solve(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver),
                                   bb.ctypes.data_as(ctypes.c_void_p), x.ctypes.data_as(ctypes.c_void_p), int(nrhs),
-                                  info, 0, None)
+                                  info, flags, None)
     _check(rc, allow=(OK, ENOCONV))
     return x, [i.as_dict() for i in info], rc
 

@@ -94,8 +94,9 @@ def test_schur_low_precision_against_fp64(lq, dims, prec, tol):
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 4e-3)])
 def test_every_kernel_shape_agrees(lq, prec, tol, monkeypatch):
     """Forces each hopping-kernel shape the autotuner can pick (two right-hand
-    sides per thread in packed FP32x2 lanes, plain or with 2/3 directions of
-    words staged in shared memory, 1-3 per thread in scalar arithmetic, or
+    sides per thread in packed FP32x2 lanes, plain, with 2/3 directions of
+    words staged in shared memory, or with links and clover prepared once per
+    32-site tile in shared memory, 1-3 per thread in scalar arithmetic, or
     one per thread with 2/4/8 directions of loads issued ahead, times groups
     per block and the super-tile block order) and checks it against FP64.
     In FP16 storage every shape computes the same per-lane arithmetic, so all
@@ -115,7 +116,8 @@ def test_every_kernel_shape_agrees(lq, prec, tol, monkeypatch):
         for dag in (False, True):
             ref = lq.schur_apply(lat, gid, dp, xt, precision="fp64", nrhs=nrhs, dagger=dag).cpu().numpy()
             for nr, gpb, swz in [(0, 1, 1), (0, 3, 1), (0, 1, 8), (1, 1, 1), (1, 5, 1), (1, 1, 8), (2, 1, 1), (2, 3, 1),
-                                 (3, 1, 32), (-2, 1, 1), (-4, 5, 1), (-8, 1, 8), (12, 1, 1), (12, 3, 1), (13, 2, 8)]:
+                                 (3, 1, 32), (-2, 1, 1), (-4, 5, 1), (-8, 1, 8), (12, 1, 1), (12, 3, 1), (13, 2, 8),
+                                 (20, 1, 1), (20, 3, 1), (21, 2, 1)]:
                 monkeypatch.setenv("LQCD_HOP_NR", str(nr))
                 monkeypatch.setenv("LQCD_HOP_GPB", str(gpb))
                 monkeypatch.setenv("LQCD_HOP_SWZ", str(swz))

@@ -56,13 +56,15 @@ def test_point_source_solve_4x4(lq, prec):
     assert rel(x, xo) <= 1e-8
 
 
-def test_fp16_solve_identical_for_every_kernel_shape(lq, monkeypatch):
+@pytest.mark.parametrize("dims", [(6, 4, 4, 8), (6, 6, 2, 6)])
+def test_fp16_solve_identical_for_every_kernel_shape(lq, monkeypatch, dims):
     """Every FP16 hopping-kernel shape computes the same per-lane arithmetic,
     and the norms go through the same per-tile partial sums, so a whole
     mixed-precision solve (with the norm-computing kernel variants) must give
-    the same bits whichever shape runs.  Three RHS on a ragged 6x4x4x8."""
+    the same bits whichever shape runs.  Three RHS on ragged lattices (6x6x2x6:
+    216 sites per parity, a partly filled 32-site tile and an empty one)."""
     import torch
-    dims, kappa, csw = (6, 4, 4, 8), 0.13, 1.5
+    kappa, csw = 0.13, 1.5
     theta = (1, np.exp(0.4j), 1, -1)
     U = inputs.gauge_field(dims, 0.4, seed=2)
     b = inputs.spinor_field(dims, seed=3, nrhs=3)
@@ -72,7 +74,7 @@ def test_fp16_solve_identical_for_every_kernel_shape(lq, monkeypatch):
         dp = lq.dirac_params(kappa, csw, theta)
         sp = lq.solver_params(tol=1e-10, maxiter=5000, precision="fp16")
         sols = {}
-        for nr, gpb in [(1, 1), (0, 1), (0, 2), (12, 1), (12, 2), (13, 1), (-4, 1), (2, 1)]:
+        for nr, gpb in [(1, 1), (0, 1), (0, 2), (12, 1), (12, 2), (13, 1), (-4, 1), (2, 1), (20, 1), (20, 2), (21, 2)]:
             monkeypatch.setenv("LQCD_HOP_NR", str(nr))
             monkeypatch.setenv("LQCD_HOP_GPB", str(gpb))
             x, info, rc = lq.cg_solve(lat, gid, dp, sp, torch.from_numpy(b).cuda(), nrhs=3)
