@@ -60,6 +60,7 @@ struct lqcd_server_s {
     std::vector<lqcd::ServeGauge> gauges;
     std::vector<std::thread> threads;
     volatile bool stop = false;
+    int pollers = 0;  // lqcd_serve_poll calls in progress (destroy waits for them)
 };
 
 namespace lqcd {
@@ -268,6 +269,16 @@ int lqcd_serve_poll(lqcd_server srv, uint64_t ticket, double *corr, lqcd_solve_i
 {
     if (!srv) return fail(LQCD_EINVAL, "null server");
     std::unique_lock<std::mutex> lk(srv->mu);
+    // counted while inside, so that lqcd_serve_destroy waits for this call to leave
+    struct Inside {
+        lqcd_server_s *s;
+        Inside(lqcd_server_s *s_) : s(s_) { ++s->pollers; }
+        ~Inside()
+        {
+            --s->pollers;
+            s->cv_done.notify_all();
+        }
+    } inside(srv);
     auto it = srv->reqs.find(ticket);
     if (it == srv->reqs.end()) return fail(LQCD_ENOTFOUND, "unknown ticket");
     ServeRequest *r = it->second.get();
@@ -292,13 +303,26 @@ int lqcd_serve_destroy(lqcd_server srv)
 {
     if (!srv) return LQCD_OK;
     {
+        // queued requests will never run: they finish now, so that a poll
+        // waiting on one of them returns instead of waiting forever
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->stop = true;
+        const double t = now_s();
+        for (ServeRequest *r : srv->queue) {
+            r->status = LQCD_ETIMEOUT;
+            r->err = "server stopped";
+            r->ts[1] = r->ts[2] = r->ts[3] = t;
+            r->done = true;
+        }
         srv->queue.clear();
     }
     srv->cv_work.notify_all();
     srv->cv_done.notify_all();
-    for (auto &t : srv->threads) t.join();
+    for (auto &t : srv->threads) t.join();  // running requests stop at their next poll and finish
+    {
+        std::unique_lock<std::mutex> lk(srv->mu);
+        srv->cv_done.wait(lk, [&] { return srv->pollers == 0; });
+    }
     for (auto &kv : srv->lattices) lqcd_lattice_destroy(kv.second);
     delete srv;
     return LQCD_OK;

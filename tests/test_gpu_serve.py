@@ -47,11 +47,13 @@ def test_served_results_equal_alone_and_oracle(lq):
                                    lq.solver_params(tol=1e-10, maxiter=5000, precision=p), src)
                    for k, kap, c, src, p in plan]
         assert len(set(tickets)) == len(tickets)
+        stamps = []
         for t, (k, kap, c, src, p) in zip(tickets, plan):
             dims = FIELDS[k][0]
             rc, corr, infos, ts = lq.serve_poll(srv, t, dims[3], timeout_ms=-1)
             assert rc == lq.OK, infos
             assert ts[0] <= ts[1] <= ts[2] <= ts[3]
+            stamps.append(ts)
             assert all(i["true_resid"] <= 1e-10 for i in infos)
             ref, *_ = oracle.pion(dims, U[k], kap, c, src, tol=1e-13)
             assert np.all(np.abs(corr - ref) <= 1e-8 * np.abs(ref)), (k, p)
@@ -70,6 +72,14 @@ def test_served_results_equal_alone_and_oracle(lq):
             assert e.value.code == lq.ENOTFOUND
     finally:
         lq.serve_destroy(srv)
+    # continuous batching, from the timestamps {arrive, admit, start, finish}:
+    # requests ran at the same time, and a slot freed by a retired request
+    # took a queued one while another request was still running
+    n = len(stamps)
+    assert any(stamps[i][2] < stamps[j][3] and stamps[j][2] < stamps[i][3]
+               for i in range(n) for j in range(i + 1, n)), stamps
+    assert any(stamps[j][3] <= stamps[i][1] and stamps[k][2] < stamps[i][1] < stamps[k][3]
+               for i in range(n) for j in range(n) for k in range(n) if len({i, j, k}) == 3), stamps
 
 
 def test_admission_by_hbm_budget(lq):
@@ -113,8 +123,23 @@ def test_poll_busy_timeout_unknown_and_shutdown(lq):
         assert e.value.code == lq.ENOTFOUND
         rc, corr, infos, ts = lq.serve_poll(srv, t1, 16, timeout_ms=-1)
         assert rc == lq.OK and np.all(corr > 0)
-        # queue more work and stop the server while it runs: destroy must return
-        for k in range(3):
-            lq.serve_submit(srv, g, lq.dirac_params(0.128, 1.5), sp, (k, 1, 0, 0))
+        # queue more work and stop the server while it runs: destroy must return,
+        # and a poll already waiting on a queued request must return too
+        import threading
+        queued = [lq.serve_submit(srv, g, lq.dirac_params(0.128, 1.5), sp, (k, 1, 0, 0)) for k in range(3)]
+        got, entering = [], threading.Event()
+
+        def wait_for_last():
+            entering.set()
+            got.append(lq.serve_poll(srv, queued[-1], 16, timeout_ms=-1)[0])
+
+        waiter = threading.Thread(target=wait_for_last)
+        waiter.start()
+        assert entering.wait(timeout=10)
+        rc, *_ = lq.serve_poll(srv, queued[-1], 16, timeout_ms=500)  # the waiter is inside its poll by now
+        assert rc == lq.ETIMEOUT  # still queued behind the running requests
     finally:
         lq.serve_destroy(srv)
+    waiter.join(timeout=60)
+    assert not waiter.is_alive()
+    assert got == [lq.ETIMEOUT]
