@@ -62,6 +62,14 @@ def _load():
                                        ctypes.POINTER(ctypes.c_double)]
         lib.oracle_pion.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.c_double, ctypes.c_int, dp, dp, ip, dp]
+        lib.oracle_dirac_open.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                          ctypes.c_int]
+        lib.oracle_cgnr_open.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                         ctypes.c_double, ctypes.c_int, ip, dp]
+        lib.oracle_cgnr_open.restype = ctypes.c_int
+        lib.oracle_boundary_corr.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                                             ctypes.c_double, ctypes.c_int, dp, dp, dp, ip, dp]
+        lib.oracle_boundary_corr.restype = ctypes.c_int
         lib.oracle_pion.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -167,6 +175,43 @@ def cgnr_tm(dims, U, kappa, csw, mu, b, theta=DEFAULT_THETA, tol=1e-13, maxiter=
     st = _load().oracle_cgnr_tm(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, mu, _dp(th),
                                 _dp(b), _dp(x), tol, maxiter, ctypes.byref(it), ctypes.byref(res))
     return x, it.value, res.value, st == 0
+
+
+def dirac_open(dims, U, kappa, csw, cF, psi, theta=DEFAULT_THETA, dagger=False) -> np.ndarray:
+    """D (or D^dag) with open boundary conditions in time and boundary coefficient cF."""
+    U, psi, th, d = _c128(U), _c128(psi), _theta(theta), _dims(dims)
+    out = np.zeros_like(psi)
+    _load().oracle_dirac_open(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, cF, _dp(th),
+                              _dp(psi), _dp(out), int(bool(dagger)))
+    return out
+
+
+def cgnr_open(dims, U, kappa, csw, cF, b, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000):
+    """Solves the open-boundary D x = b by CGNR; returns (x, iterations, true relative residual, converged)."""
+    U, b, th, d = _c128(U), _c128(b), _theta(theta), _dims(dims)
+    x = np.zeros_like(b)
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0)
+    st = _load().oracle_cgnr_open(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, cF, _dp(th),
+                                  _dp(b), _dp(x), tol, maxiter, ctypes.byref(it), ctypes.byref(res))
+    return x, it.value, res.value, st == 0
+
+
+def boundary_corr(dims, U, kappa, csw, cF, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000, want_prop=False):
+    """Open-boundary f_P(x_t), f_A(x_t) from the six P+ wall sources on slice 0.
+
+    Returns (fP, fA, H or None [6, T, Z, Y, X, 4, 3], iterations[6], residuals[6], failed_columns)."""
+    lx, ly, lz, lt = dims
+    U, th, d = _c128(U), _theta(theta), _dims(dims)
+    fP, fA = np.zeros(lt), np.zeros(lt)
+    H = np.zeros((6, lt, lz, ly, lx, 4, 3), dtype=np.complex128) if want_prop else None
+    iters = np.zeros(6, dtype=np.int32)
+    res = np.zeros(6)
+    failed = _load().oracle_boundary_corr(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, cF,
+                                          _dp(th), tol, maxiter, _dp(fP), _dp(fA),
+                                          _dp(H) if H is not None else None,
+                                          iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(res))
+    return fP, fA, H, iters, res, failed
 
 
 def pion_contract(dims, prop, src_t) -> np.ndarray:

@@ -291,6 +291,9 @@ typedef struct {
     double mu; /* twisted mass (mass units): site term + 2 i kappa mu g5; 0 for the Wilson-clover D */
     cplx theta[4];
     double *F; /* clover field F[site][plane][3][3], NULL when csw == 0 */
+    int open;   /* open boundary in time: the links U_t(x) with x_t = T - 1 are absent */
+    double cF;  /* boundary improvement coefficient on the slices x_t = 0 and T - 1 (open only) */
+    double *Uopen; /* the gauge field with the absent links set to zero (owned; open only) */
 } dirac_ctx;
 
 static void ctx_init(dirac_ctx *c, const int *L, const double *U, double kappa, double csw,
@@ -304,13 +307,41 @@ static void ctx_init(dirac_ctx *c, const int *L, const double *U, double kappa, 
     c->mu = 0.0;
     for (int mu = 0; mu < 4; ++mu) c->theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
     c->F = NULL;
+    c->open = 0;
+    c->cF = 1.0;
+    c->Uopen = NULL;
     if (csw != 0.0) {
         c->F = malloc(sizeof(double) * 108 * volume_of(L));
         oracle_field_strength(L, U, c->F);
     }
 }
 
-static void ctx_free(dirac_ctx *c) { free(c->F); c->F = NULL; }
+/* Open boundary conditions in time (Sec. 2.1, BC_OPEN): the lattice has no
+ * link from the slice x_t = T - 1 to x_t = 0.  Read plainly: that link is
+ * zero, so every hop across the time boundary and every clover leaf through
+ * it vanish; the slices x_t = 0 and T - 1 get the boundary improvement term
+ * (cF - 1) of D_w, i.e. 2 kappa (cF - 1) in the kappa normalisation (cF of
+ * DiracParam, Sec. 3.3). */
+static void ctx_init_open(dirac_ctx *c, const int *L, const double *U, double kappa, double csw,
+                          const double *theta, double cF)
+{
+    long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2];
+    double *Uz = malloc(sizeof(double) * 72 * V);
+    memcpy(Uz, U, sizeof(double) * 72 * V);
+    for (long s = (long)(L[3] - 1) * V3; s < V; ++s) memset(Uz + 18 * (4 * s + 3), 0, sizeof(double) * 18);
+    ctx_init(c, L, Uz, kappa, csw, theta);
+    c->Uopen = Uz;
+    c->open = 1;
+    c->cF = cF;
+}
+
+static void ctx_free(dirac_ctx *c)
+{
+    free(c->F);
+    c->F = NULL;
+    free(c->Uopen);
+    c->Uopen = NULL;
+}
 
 static mat3 stored_F(const dirac_ctx *c, long x, int p)
 {
@@ -360,6 +391,12 @@ static spinor dirac_site(const dirac_ctx *c, const double *psi, long x)
         for (int al = 0; al < 4; ++al)
             for (int a = 0; a < 3; ++a) out.c[al][a] += 2.0 * I * c->kappa * c->mu * G[4][al][al] * s.c[al][a];
     }
+    if (c->open && (xc[3] == 0 || xc[3] == L[3] - 1)) {
+        /* boundary improvement: + 2 kappa (cF - 1) psi(x) on the first and last slice */
+        spinor s = spinor_at(psi, x);
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) out.c[al][a] += 2.0 * c->kappa * (c->cF - 1.0) * s.c[al][a];
+    }
     return out;
 }
 
@@ -405,6 +442,11 @@ static void dirac_dagger_apply(const dirac_ctx *c, const double *in, double *out
             for (int al = 0; al < 4; ++al)
                 for (int a = 0; a < 3; ++a)
                     acc[x].c[al][a] += -2.0 * I * c->kappa * c->mu * G[4][al][al] * px.c[al][a];
+        }
+        if (c->open && (xc[3] == 0 || xc[3] == L[3] - 1)) {
+            /* the boundary term is real and diagonal: its own adjoint */
+            for (int al = 0; al < 4; ++al)
+                for (int a = 0; a < 3; ++a) acc[x].c[al][a] += 2.0 * c->kappa * (c->cF - 1.0) * px.c[al][a];
         }
         for (int mu = 0; mu < 4; ++mu) {
             /* term D(x, x+mu) = -kappa (1 - g_mu) U~_mu(x): adjoint goes to x+mu */
@@ -606,6 +648,87 @@ int oracle_cgnr_tm(const int *L, const double *U, double kappa, double csw, doub
     int st = cgnr_ctx(&c, L, b, x, tol, maxiter, iters, resid);
     ctx_free(&c);
     return st;
+}
+
+/* The operator with open boundary conditions in time (see ctx_init_open):
+ * D or D^dag on the T slices of the lattice, theta_t playing no part. */
+void oracle_dirac_open(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                       const double *in, double *out, int dagger)
+{
+    dirac_ctx c;
+    ctx_init_open(&c, L, U, kappa, csw, theta, cF);
+    if (dagger)
+        dirac_dagger_apply(&c, in, out);
+    else
+        dirac_apply(&c, in, out);
+    ctx_free(&c);
+}
+
+/* CGNR of oracle_cgnr on the open-boundary operator */
+int oracle_cgnr_open(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                     const double *b, double *x, double tol, int maxiter, int *iters, double *resid)
+{
+    dirac_ctx c;
+    ctx_init_open(&c, L, U, kappa, csw, theta, cF);
+    int st = cgnr_ctx(&c, L, b, x, tol, maxiter, iters, resid);
+    ctx_free(&c);
+    return st;
+}
+
+/* Boundary-to-bulk correlators with open boundaries (Sec. 3.3: the
+ * propagators from the boundary that give f_P and f_A).  Read as: the six
+ * sources W_j(y) = delta_{y_t, 0} P+ e_j, j = 3 s + c with spin s in {0, 1}
+ * and colour c, P+ = (1 + g_t) / 2, on every site of the boundary slice
+ * (zero spatial momentum); H_j = D^-1 W_j; then per slice x_t
+ *   fP[x_t] = sum_xvec sum_j |H_j(x)|^2,
+ *   fA[x_t] = - sum_xvec sum_j Re <H_j(x), g_t H_j(x)>   (spin-colour inner product).
+ * (P+ e_{j+6} = -P+ e_j, so the six columns are all there is.)  H (may be
+ * NULL) receives the columns [6][site][12] complex; iters, resid (may be
+ * NULL) per column.  Returns the number of columns that did not converge. */
+int oracle_boundary_corr(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                         double tol, int maxiter, double *fP, double *fA, double *H, int *iters, double *resid)
+{
+    init_gamma();
+    const long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2], n = 24 * V;
+    double *S = H ? H : malloc(sizeof(double) * 6 * n);
+    double *w = calloc((size_t)n, sizeof(double));
+    dirac_ctx c;
+    ctx_init_open(&c, L, U, kappa, csw, theta, cF);
+    int failed = 0;
+    for (int j = 0; j < 6; ++j) {
+        memset(w, 0, sizeof(double) * n);
+        for (long y = 0; y < V3; ++y)       /* the slice y_t = 0 */
+            for (int al = 0; al < 4; ++al) { /* (P+ e_j)_al = (delta_{al,s} + (g_t)_{al,s}) / 2 */
+                const int s = j / 3, col = j % 3;
+                cplx v = 0.5 * ((al == s ? 1.0 : 0.0) + G[3][al][s]);
+                w[24 * y + 2 * (3 * al + col)] = creal(v);
+                w[24 * y + 2 * (3 * al + col) + 1] = cimag(v);
+            }
+        double *x = S + (long)j * n;
+        memset(x, 0, sizeof(double) * n);
+        int it;
+        double res;
+        failed += cgnr_ctx(&c, L, w, x, tol, maxiter, &it, &res);
+        if (iters) iters[j] = it;
+        if (resid) resid[j] = res;
+    }
+    for (int t = 0; t < L[3]; ++t) fP[t] = fA[t] = 0.0;
+    for (int j = 0; j < 6; ++j)
+        for (long x = 0; x < V; ++x) {
+            const int t = (int)(x / V3);
+            spinor h = spinor_at(S + (long)j * n, x);
+            for (int al = 0; al < 4; ++al)
+                for (int a = 0; a < 3; ++a) {
+                    cplx gh = 0;
+                    for (int be = 0; be < 4; ++be) gh += G[3][al][be] * h.c[be][a];
+                    fP[t] += creal(conj(h.c[al][a]) * h.c[al][a]);
+                    fA[t] -= creal(conj(h.c[al][a]) * gh);
+                }
+        }
+    ctx_free(&c);
+    free(w);
+    if (!H) free(S);
+    return failed;
 }
 
 /* ------------------------------------------------------------------ */

@@ -567,3 +567,122 @@ def test_dirac_sites_equals_full_operator(dims, eps, kappa, csw, theta):
     dag = oracle.dirac(dims, U, kappa, csw, psi, theta=theta, dagger=True).reshape(V, 4, 3)
     g5d = np.einsum("ab,kbc->kac", G5, oracle.dirac_sites(dims, U, kappa, csw, g5(psi), sites, theta=theta))
     assert np.max(np.abs(g5d - dag)) <= 1e-14 * np.max(np.abs(dag))
+
+
+# --------------------------------------------------------------------------
+# open boundary conditions in time and the boundary-to-bulk correlators
+# --------------------------------------------------------------------------
+
+def _time_matrix(T, kappa, cF, p):
+    """(4T x 4T) matrix of the free open-boundary operator on e^{i p.x} f(x_t)
+    spinors (colour trivial), from the momentum-space form: site term
+    1 - kappa sum_k (2 cos p_k - 2 i g_k sin p_k) + 2 kappa (cF - 1) on x_t in
+    {0, T-1}; time hops -kappa (1 - g_t) to t+1 and -kappa (1 + g_t) to t-1, no wrap."""
+    g = BASIS
+    I4 = np.eye(4)
+    site = I4 * 1.0 + 0j
+    for k in range(3):
+        site = site - kappa * (2 * np.cos(p[k]) * I4 - 2j * np.sin(p[k]) * g[k])
+    M = np.zeros((4 * T, 4 * T), complex)
+    for t in range(T):
+        M[4 * t:4 * t + 4, 4 * t:4 * t + 4] = site + (2 * kappa * (cF - 1) * I4 if t in (0, T - 1) else 0)
+        if t + 1 < T:
+            M[4 * t:4 * t + 4, 4 * (t + 1):4 * t + 8] = -kappa * (I4 - g[3])
+        if t - 1 >= 0:
+            M[4 * t:4 * t + 4, 4 * (t - 1):4 * t] = -kappa * (I4 + g[3])
+    return M
+
+
+def test_open_free_field_plane_waves_in_space():
+    """Unit links, twisted spatial phases: e^{i p.x} f(x_t) with p_k =
+    (arg theta_k + 2 pi n_k) / L_k is mapped to e^{i p.x} (M_p f)(x_t)."""
+    dims = (4, 6, 2, 7)
+    kappa, cF = 0.13, 1.37
+    theta = (np.exp(0.4j), np.exp(-1.1j), 1.0, np.exp(0.9j))  # theta_t plays no part
+    U = inputs.unit_gauge_field(dims)
+    rng = np.random.default_rng(5)
+    x, y, z = np.meshgrid(np.arange(dims[0]), np.arange(dims[1]), np.arange(dims[2]), indexing="ij")
+    for n in [(0, 0, 0), (1, 2, 1), (3, 5, 0)]:
+        p = [(np.angle(theta[k]) + 2 * np.pi * n[k]) / dims[k] for k in range(3)]
+        f = rng.normal(size=(dims[3], 4)) + 1j * rng.normal(size=(dims[3], 4))
+        wave = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z)).transpose(2, 1, 0)  # [z, y, x]
+        col = rng.normal(size=3) + 1j * rng.normal(size=3)
+        psi = np.einsum("zyx,ts,c->tzyxsc", wave, f, col)
+        Mf = (_time_matrix(dims[3], kappa, cF, p) @ f.reshape(-1)).reshape(dims[3], 4)
+        want = np.einsum("zyx,ts,c->tzyxsc", wave, Mf, col)
+        for csw in (0.0, 1.9):  # the clover term vanishes at unit links, also at the boundary
+            got = oracle.dirac_open(dims, U, kappa, csw, cF, psi, theta=theta)
+            assert rel(got, want) < 1e-14
+
+
+def test_open_boundary_to_bulk_free_field():
+    """f_P, f_A at unit links: the wall sources have zero spatial momentum,
+    so H_j(x) = h_j(x_t) with M_0 h_j = delta_{t,0} P+ e_j, and the sums over
+    xvec give L^3 times the slice values."""
+    dims = (4, 4, 2, 6)
+    kappa, cF = 0.12, 0.8
+    T, L3 = dims[3], dims[0] * dims[1] * dims[2]
+    U = inputs.unit_gauge_field(dims)
+    fP, fA, H, iters, res, failed = oracle.boundary_corr(dims, U, kappa, 1.0, cF, tol=1e-13)
+    assert failed == 0
+    M = _time_matrix(T, kappa, cF, (0.0, 0.0, 0.0))
+    Pp = 0.5 * (np.eye(4) + BASIS[3])
+    wantP, wantA = np.zeros(T), np.zeros(T)
+    for s in range(2):
+        src = np.zeros(4 * T, complex)
+        src[0:4] = Pp[:, s]
+        h = np.linalg.solve(M, src).reshape(T, 4)
+        for t in range(T):  # three colours, each the same spin vector
+            wantP[t] += 3 * L3 * np.vdot(h[t], h[t]).real
+            wantA[t] -= 3 * L3 * np.vdot(h[t], BASIS[3] @ h[t]).real
+    assert np.allclose(fP, wantP, rtol=1e-11, atol=0)
+    assert np.allclose(fA, wantA, rtol=1e-10, atol=1e-12 * np.max(np.abs(wantP)))
+
+
+def _zero_boundary_links(dims, U):
+    Uz = U.copy()
+    Uz[dims[3] - 1, ..., 3, :, :] = 0
+    return Uz
+
+
+def test_open_operator_identities_on_rough_fields():
+    """Rough field with clover: the open operator is the periodic operator of
+    the field whose time links leaving the last slice are zero, plus
+    2 kappa (cF - 1) on the first and last slice; gamma5-hermiticity, the
+    adjoint identity and gauge covariance hold; interior slices see the
+    periodic clover term."""
+    dims = (4, 4, 2, 6)
+    kappa, csw, cF = 0.125, 1.6, 1.3
+    T = dims[3]
+    U = inputs.gauge_field(dims, 0.5, seed=41)
+    a = inputs.spinor_field(dims, seed=42)
+    b = inputs.spinor_field(dims, seed=43)
+    th = (np.exp(0.3j), 1, 1, np.exp(1.2j))
+    D = lambda v, dag=False, UU=U: oracle.dirac_open(dims, UU, kappa, csw, cF, v, theta=th, dagger=dag)
+    bmask = np.zeros(dims[::-1])[..., None, None]
+    bmask[0] = bmask[T - 1] = 1.0
+    per = oracle.dirac(dims, _zero_boundary_links(dims, U), kappa, csw, a, theta=th)
+    assert rel(D(a), per + 2 * kappa * (cF - 1) * bmask * a) < 1e-14
+    assert abs(vdot(a, D(b)) - vdot(g5(D(g5(a))), b)) <= 1e-14 * abs(vdot(a, D(b)))
+    assert abs(vdot(a, D(b)) - vdot(D(a, True), b)) <= 1e-14 * abs(vdot(a, D(b)))
+    g = inputs.gauge_transform(dims, seed=44)
+    Ug = _transform(U, g)
+    assert rel(D(np.einsum("...ab,...sb->...sa", g, a), UU=Ug), np.einsum("...ab,...sb->...sa", g, D(a))) < 1e-14
+    # clover part away from the boundary slices equals the periodic one
+    dc = D(a) - oracle.dirac_open(dims, U, kappa, 0.0, cF, a, theta=th)
+    dp = oracle.dirac(dims, U, kappa, csw, a, theta=th) - oracle.dirac(dims, U, kappa, 0.0, a, theta=th)
+    assert rel(dc[1:T - 1], dp[1:T - 1]) < 1e-13
+    assert rel(dc[0], dp[0]) > 1e-3  # leaves through the missing links are gone
+
+
+def test_open_cgnr_matches_dense_inverse():
+    dims = (2, 2, 2, 4)
+    kappa, csw, cF = 0.13, 1.4, 1.2
+    U = inputs.gauge_field(dims, 0.4, seed=45)
+    b = inputs.spinor_field(dims, seed=46)
+    n = 12 * int(np.prod(dims))
+    cols = np.eye(n, dtype=complex).reshape((n,) + tuple(dims[::-1]) + (4, 3))
+    M = np.stack([oracle.dirac_open(dims, U, kappa, csw, cF, c).reshape(-1) for c in cols], axis=1)
+    want = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
+    x, it, res, ok = oracle.cgnr_open(dims, U, kappa, csw, cF, b, tol=1e-13)
+    assert ok and rel(x, want) < 1e-11
