@@ -503,12 +503,13 @@ void oracle_dirac_sites(const int *L, const double *U, double kappa, double csw,
                         double *out)
 {
     dirac_ctx c;
+    memset(&c, 0, sizeof c); /* the periodic Wilson-clover D: no twist, no open boundary */
     init_gamma();
     memcpy(c.L, L, sizeof c.L);
     c.U = U;
     c.kappa = kappa;
     c.csw = csw;
-    c.mu = 0.0; /* the Wilson-clover D: no twisted-mass term */
+    c.cF = 1.0;
     for (int mu = 0; mu < 4; ++mu) c.theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
     double Fx[108];
     for (long k = 0; k < nsites; ++k) {
