@@ -70,6 +70,8 @@ def _load():
         lib.oracle_boundary_corr.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                              ctypes.c_double, ctypes.c_int, dp, dp, dp, ip, dp]
         lib.oracle_boundary_corr.restype = ctypes.c_int
+        lib.oracle_gauge_obs.argtypes = [ip, dp, dp, dp, dp, dp]
+        lib.oracle_wilson_flow.argtypes = [ip, dp, ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_pion.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -212,6 +214,27 @@ def boundary_corr(dims, U, kappa, csw, cF, theta=DEFAULT_THETA, tol=1e-13, maxit
                                           _dp(H) if H is not None else None,
                                           iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(res))
     return fP, fA, H, iters, res, failed
+
+
+def gauge_obs(dims, U):
+    """(plaquette average, Eplaq[T], Eclov[T], Q[T]): per-slice sums of the action density
+    (plaquette and clover) and of the clover topological charge density."""
+    U, d = _c128(U), _dims(dims)
+    T = dims[3]
+    plaq = ctypes.c_double(0)
+    Ep, Ec, Q = np.zeros(T), np.zeros(T), np.zeros(T)
+    _load().oracle_gauge_obs(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), ctypes.byref(plaq), _dp(Ep),
+                             _dp(Ec), _dp(Q))
+    return plaq.value, Ep, Ec, Q
+
+
+def wilson_flow(dims, U, eps, nsteps) -> np.ndarray:
+    """The gauge field after nsteps RK3 Wilson-flow steps of size eps."""
+    U, d = _c128(U), _dims(dims)
+    out = np.zeros_like(U)
+    _load().oracle_wilson_flow(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), float(eps), int(nsteps),
+                               _dp(out))
+    return out
 
 
 def pion_contract(dims, prop, src_t) -> np.ndarray:

@@ -42,6 +42,8 @@
 
 typedef double complex cplx;
 
+static const double PI = 3.14159265358979323846;
+
 /* ------------------------------------------------------------------ */
 /* Lattice geometry (Sec. 2.1: iL with the time extent last)           */
 /* ------------------------------------------------------------------ */
@@ -730,6 +732,149 @@ int oracle_boundary_corr(const int *L, const double *U, double kappa, double csw
     free(w);
     if (!H) free(S);
     return failed;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gauge observables and the Wilson flow (Sec. 3.2)                    */
+/* ------------------------------------------------------------------ */
+
+static mat3 scale3(mat3 a, cplx s)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) a.m[i][j] *= s;
+    return a;
+}
+
+static cplx trace3(mat3 a) { return a.m[0][0] + a.m[1][1] + a.m[2][2]; }
+
+/* U_p = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag */
+static mat3 plaquette_at(const int L[4], const double *U, long x, int mu, int nu)
+{
+    long xpm = step(L, x, mu, +1), xpn = step(L, x, nu, +1);
+    return mul(mul(link_at(U, x, mu), link_at(U, xpm, nu)), mul(dag(link_at(U, xpn, mu)), dag(link_at(U, x, nu))));
+}
+
+/* Gauge observables (plaquette, Eoft_plaq, Eoft_clover, Qtop of Sec. 3.2):
+ *   plaq       = (1 / 6V) sum_x sum_{mu<nu} Re tr U_p / 3  (1 for the unit field);
+ *   Eplaq[t]   = sum_xvec 2 sum_{mu<nu} Re tr (1 - U_p(x))  (the plaquette action density, summed per slice);
+ *   Eclov[t]   = sum_xvec - sum_{mu<nu} tr F_{mu nu}(x)^2  (F the antihermitian clover field above);
+ *   Q[t]       = sum_xvec - (1 / 32 pi^2) eps_{mu nu rho sigma} tr F_{mu nu}(x) F_{rho sigma}(x),
+ * the epsilon sum written out as 8 [tr F_xy F_zt - tr F_xz F_yt + tr F_xt F_yz]. */
+void oracle_gauge_obs(const int *L, const double *U, double *plaq, double *Eplaq, double *Eclov, double *Q)
+{
+    const long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2];
+    double psum = 0.0;
+    for (int t = 0; t < L[3]; ++t) Eplaq[t] = Eclov[t] = Q[t] = 0.0;
+    for (long x = 0; x < V; ++x) {
+        const int t = (int)(x / V3);
+        mat3 F[6];
+        for (int p = 0; p < 6; ++p) {
+            const int mu = PLANE[p][0], nu = PLANE[p][1];
+            const double re = creal(trace3(plaquette_at(L, U, x, mu, nu)));
+            psum += re / 3.0;
+            Eplaq[t] += 2.0 * (3.0 - re);
+            F[p] = field_strength(L, U, x, mu, nu);
+            Eclov[t] -= creal(trace3(mul(F[p], F[p])));
+        }
+        /* planes (x,y) (x,z) (x,t) (y,z) (y,t) (z,t) = 0..5 */
+        const double e = creal(trace3(mul(F[0], F[5]))) - creal(trace3(mul(F[1], F[4]))) +
+                         creal(trace3(mul(F[2], F[3])));
+        Q[t] -= 8.0 * e / (32.0 * PI * PI);
+    }
+    *plaq = psum / (6.0 * V);
+}
+
+/* exp(X) by its Taylor series, summed until the terms stop changing the sum */
+static mat3 expm3(mat3 X)
+{
+    mat3 r, term;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) r.m[i][j] = term.m[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int k = 1; k < 60; ++k) {
+        term = scale3(mul(term, X), 1.0 / k);
+        double n = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                r.m[i][j] += term.m[i][j];
+                n += creal(term.m[i][j] * conj(term.m[i][j]));
+            }
+        if (n < 1e-40) break;
+    }
+    return r;
+}
+
+/* The flow generator Z_mu(x) = -d_{x,mu} S(U) for the Wilson action summed
+ * over oriented plaquettes, S = 2 sum_{mu<nu} Re tr (1 - U_p) (Luescher's
+ * normalisation of the Wilson flow, cited by Sec. 3.2): with the staple sum
+ * S_mu(x) such that Omega = U_mu(x) S_mu(x) closes every plaquette through
+ * the link, Z = -(1/2) (Omega - Omega^dag) + (1/6) tr (Omega - Omega^dag). */
+static mat3 flow_generator(const int L[4], const double *U, long x, int mu)
+{
+    mat3 S;
+    memset(&S, 0, sizeof S);
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        long xpm = step(L, x, mu, +1), xpn = step(L, x, nu, +1), xmn = step(L, x, nu, -1);
+        long xpm_mn = step(L, xpm, nu, -1);
+        S = add(S, mul(mul(link_at(U, xpm, nu), dag(link_at(U, xpn, mu))), dag(link_at(U, x, nu))));
+        S = add(S, mul(mul(dag(link_at(U, xpm_mn, nu)), dag(link_at(U, xmn, mu))), link_at(U, xmn, nu)));
+    }
+    mat3 om = mul(link_at(U, x, mu), S), Z;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Z.m[i][j] = -0.5 * (om.m[i][j] - conj(om.m[j][i]));
+    cplx tr = trace3(Z) / 3.0;
+    for (int i = 0; i < 3; ++i) Z.m[i][i] -= tr;
+    return Z;
+}
+
+static void store_link(double *U, long s, int mu, mat3 m)
+{
+    double *p = U + 18 * (4 * s + mu);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            p[2 * (3 * a + b)] = creal(m.m[a][b]);
+            p[2 * (3 * a + b) + 1] = cimag(m.m[a][b]);
+        }
+}
+
+/* Wilson flow (Sec. 3.2, flw with the wfl_rk3 scheme): nsteps steps of size
+ * eps of the third-order Runge-Kutta integrator of Luescher (JHEP 2010):
+ *   W1 = exp(Z0/4) W0,  W2 = exp(8 Z1/9 - 17 Z0/36) W1,
+ *   V(t + eps) = exp(3 Z2/4 - 8 Z1/9 + 17 Z0/36) W2,   Z_i = eps Z(W_i),
+ * every link updated together at each stage.  U in, Uout out (may alias). */
+void oracle_wilson_flow(const int *L, const double *U, double eps, int nsteps, double *Uout)
+{
+    const long V = volume_of(L), n = 72 * V;
+    double *W = malloc(sizeof(double) * n);
+    mat3 *Z0 = malloc(sizeof(mat3) * 4 * V), *Z1 = malloc(sizeof(mat3) * 4 * V), *Z2 = malloc(sizeof(mat3) * 4 * V);
+    memcpy(W, U, sizeof(double) * n);
+    for (int k = 0; k < nsteps; ++k) {
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) Z0[4 * x + mu] = scale3(flow_generator(L, W, x, mu), eps);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu)
+                store_link(W, x, mu, mul(expm3(scale3(Z0[4 * x + mu], 0.25)), link_at(W, x, mu)));
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) Z1[4 * x + mu] = scale3(flow_generator(L, W, x, mu), eps);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) {
+                mat3 X = add(scale3(Z1[4 * x + mu], 8.0 / 9.0), scale3(Z0[4 * x + mu], -17.0 / 36.0));
+                store_link(W, x, mu, mul(expm3(X), link_at(W, x, mu)));
+            }
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) Z2[4 * x + mu] = scale3(flow_generator(L, W, x, mu), eps);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) {
+                mat3 X = add(add(scale3(Z2[4 * x + mu], 0.75), scale3(Z1[4 * x + mu], -8.0 / 9.0)),
+                             scale3(Z0[4 * x + mu], 17.0 / 36.0));
+                store_link(W, x, mu, mul(expm3(X), link_at(W, x, mu)));
+            }
+    }
+    memcpy(Uout, W, sizeof(double) * n);
+    free(W);
+    free(Z0);
+    free(Z1);
+    free(Z2);
 }
 
 /* ------------------------------------------------------------------ */

@@ -686,3 +686,90 @@ def test_open_cgnr_matches_dense_inverse():
     want = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
     x, it, res, ok = oracle.cgnr_open(dims, U, kappa, csw, cF, b, tol=1e-13)
     assert ok and rel(x, want) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# gauge observables and the Wilson flow
+# --------------------------------------------------------------------------
+
+def test_flow_and_observables_of_the_unit_field():
+    dims = (4, 2, 4, 6)
+    U = inputs.unit_gauge_field(dims)
+    assert np.array_equal(oracle.wilson_flow(dims, U, 0.05, 3), U)
+    plaq, Ep, Ec, Q = oracle.gauge_obs(dims, U)
+    assert plaq == 1.0 and not Ep.any() and not Ec.any() and not Q.any()
+
+
+def test_observables_two_constant_abelian_fluxes():
+    """Constant commuting fluxes in the (x,y) and (z,t) planes: the plaquette,
+    the plaquette and clover action densities and the clover charge have
+    closed forms (F_xy = i sin(phi1) T1', F_zt = i sin(phi2) T2', T' traceless)."""
+    dims = (4, 6, 4, 6)
+    T1, T2 = (1.0, -1.0, 0.0), (1.0, 0.0, 0.0)
+    U, phi1 = _abelian_field(dims, 0, 1, T1, n=1)
+    U2, phi2 = _abelian_field(dims, 2, 3, T2, n=1)
+    U[..., 3, :, :] = U2[..., 3, :, :]
+    V3 = dims[0] * dims[1] * dims[2]
+    t1 = np.diag(T1) - np.trace(np.diag(T1)) / 3 * np.eye(3)
+    t2 = np.diag(T2) - np.trace(np.diag(T2)) / 3 * np.eye(3)
+    rt1 = np.sum(np.cos(phi1 * np.array(T1)))  # Re tr exp(i phi T)
+    rt2 = np.sum(np.cos(phi2 * np.array(T2)))
+    plaq, Ep, Ec, Q = oracle.gauge_obs(dims, U)
+    assert abs(plaq - ((rt1 + rt2) / 3 + 4) / 6) < 1e-15
+    assert np.allclose(Ep, V3 * 2 * ((3 - rt1) + (3 - rt2)), rtol=1e-13, atol=0)
+    wantE = V3 * (np.sin(phi1) ** 2 * np.trace(t1 @ t1) + np.sin(phi2) ** 2 * np.trace(t2 @ t2))
+    assert np.allclose(Ec, wantE, rtol=1e-13, atol=0)
+    wantQ = V3 * np.sin(phi1) * np.sin(phi2) * np.trace(t1 @ t2) / (4 * np.pi ** 2)
+    assert np.allclose(Q, wantQ, rtol=1e-12, atol=0)
+
+
+def _diag_field(dims, theta):
+    """U_mu(x) = diag(e^{i theta_mu(x)}, e^{-i theta_mu(x)}, 1); theta[t, z, y, x, mu]."""
+    U = np.zeros(tuple(dims[::-1]) + (4, 3, 3), complex)
+    U[..., 0, 0] = np.exp(1j * theta)
+    U[..., 1, 1] = np.exp(-1j * theta)
+    U[..., 2, 2] = 1.0
+    return U
+
+
+def test_flow_normalisation_on_a_weak_abelian_wave():
+    """A weak transverse abelian wave theta_mu(x) = a cos(p.x) (polarisation
+    with p_mu = 0) decays under the flow as theta' = -phat^2 theta, phat^2 =
+    sum 4 sin^2(p/2); each RK3 step multiplies it by the third-order Taylor
+    polynomial of exp(-phat^2 eps)."""
+    dims = (6, 4, 4, 8)
+    x = _coords(dims)
+    a, eps, n = 1e-5, 0.07, 5
+    for mu_pol, p in [(1, (2 * np.pi / 6, 0, 0, 0)), (0, (0, 2 * np.pi / 4, 0, 2 * 2 * np.pi / 8))]:
+        phase = sum(p[m] * x[m] for m in range(4))
+        theta = np.zeros(tuple(dims[::-1]) + (4,))
+        theta[..., mu_pol] = a * np.cos(phase)
+        Uf = oracle.wilson_flow(dims, _diag_field(dims, theta), eps, n)
+        lam = sum(4 * np.sin(q / 2) ** 2 for q in p) * eps
+        g = (1 - lam + lam ** 2 / 2 - lam ** 3 / 6) ** n
+        got = np.angle(Uf[..., 0, 0])
+        assert np.max(np.abs(got - g * theta)) <= 1e-9 * a
+        assert np.max(np.abs(np.angle(Uf[..., 1, 1]) + got)) <= 1e-15 + 1e-9 * a
+        assert np.max(np.abs(Uf[..., 2, 2] - 1)) < 1e-14
+
+
+def test_flow_is_third_order_covariant_unitary_and_lowers_the_action():
+    dims = (4, 4, 2, 4)
+    U = inputs.gauge_field(dims, 0.3, seed=61)
+    t = 0.24
+    ref = oracle.wilson_flow(dims, U, t / 192, 192)
+    errs = [np.max(np.abs(oracle.wilson_flow(dims, U, t / n, n) - ref)) for n in (6, 12, 24)]
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 7.0 < e1 / e2 < 11.0, errs  # ~2^3 per halving: third order (second order gives ~4)
+    Uf = oracle.wilson_flow(dims, U, 0.02, 5)
+    uu = np.einsum("...ba,...bc->...ac", Uf.conj(), Uf)
+    assert np.max(np.abs(uu - np.eye(3))) < 1e-13
+    assert np.max(np.abs(np.linalg.det(Uf) - 1)) < 1e-13
+    g = inputs.gauge_transform(dims, seed=62)
+    gd = np.conj(np.swapaxes(g, -1, -2))
+    flowed_g = oracle.wilson_flow(dims, _transform(U, g), 0.02, 5)
+    assert np.max(np.abs(flowed_g - _transform(Uf, g))) < 1e-13
+    S = [np.sum(oracle.gauge_obs(dims, oracle.wilson_flow(dims, U, 0.02, k))[1]) for k in range(0, 6)]
+    assert all(b < a for a, b in zip(S, S[1:]))
+    assert abs(np.sum(oracle.gauge_obs(dims, _transform(U, g))[1]) - S[0]) < 1e-12 * S[0]
+    del gd
