@@ -43,7 +43,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Dslash HBM GB/s (%peak); mixed-vs-FP64 solves/s at 1e-10; served p50/p99"
 WORKLOAD = {
-    "workload": "pion propagator 32^3x64, 12 RHS batched, FP16 storage / FP32 math / FP64 outer, tol 1e-10",
+    "workload": "pion propagator 32^3x64, 12 RHS, FP16 store / FP32 math / FP64 outer, tol 1e-10",
     "lattice": [32, 32, 32, 64],
     "eps": 0.4,
     "kappa": 0.132,
@@ -53,16 +53,18 @@ WORKLOAD = {
     "nrhs": 12,
     "tol": 1e-10,
     "precision": "fp16",
-    "l2": "inputs larger than L2 (~10 GB working set vs 129 MB L2); no flush needed",
+    "l2": "inputs > L2 (~25 GB working set), no flush",
 }
 NOMINAL_HBM_GBS = 8000.0
-# FP32 (CUDA-core) peak derived from the unit counts and clock: 152 SMs x 128
-# FP32 lanes x 2 flop per fma x 2.07 GHz maximum SM clock.
-NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # algorithmic flops per output site and RHS: hopping term 1320, clover
 # block pair 504, plus kappa scaling (hopclov, 24) or the combination with
 # the self term (selfclov, 48)
 HOP_FLOPS = {"hop_f16_hopclov": 1320 + 504 + 24, "hop_f16_selfclov": 1320 + 504 + 48}
+# algorithmic bytes of the FP16 hopping kernels per output site: per active
+# RHS (spinor in + out, + self for selfclov: 52 B each) and shared by the
+# RHS of a launch (8 reconstruct-12 links of 24 B, one clover pair of 144 B)
+HOP_BYTES_PER_RHS = {"hop_f16_hopclov": 104.0, "hop_f16_selfclov": 156.0}
+HOP_BYTES_SHARED = {"hop_f16_hopclov": 336.0, "hop_f16_selfclov": 336.0}
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
 # one ncu capture (24^3x48, 331776 sites per parity, staged paired kernel;
 # its summary is kept under profiles/): 509.2 MB for hopclov and 722.9 MB
@@ -86,6 +88,34 @@ def kernel_digest():
 # workload (about 400 on GB300 at 32^3x64); the oracle's unpreconditioned
 # CGNR needs more, so the baseline over-states the oracle's speed.
 ORACLE_ITERS = 360
+
+
+def bench_config(world):
+    """The workload both arms report (the implementation is described elsewhere)."""
+    return {**{k: WORKLOAD[k] for k in ("workload", "lattice", "eps", "kappa", "csw", "seed", "src", "nrhs", "tol",
+                                        "precision", "l2")},
+            "parallelism": f"replicas x{world} (independent propagators)"}
+
+
+def r4(x):
+    """Rounds floats (recursively) to 4 significant digits to keep the JSON line short."""
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: r4(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [r4(v) for v in x]
+    return x
+
+
+def fp32_peak_tflops():
+    """FP32 CUDA-core roof from the device's SM count: SMs x 128 lanes x 2 flop x 2.07 GHz."""
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:  # noqa: BLE001
+        sms = 152
+    return sms * 128 * 2 * 2.07e9 / 1e12, sms
 
 
 def peaks():
@@ -197,28 +227,102 @@ def max_over_ranks(v, world):
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands
 # ---------------------------------------------------------------------------
-def cpu_baseline_measure(U, sample_frac=0.25):
-    """Times the oracle's D at a fixed quarter of the sites of the workload.
-
-    The oracle's full D computes the clover field at every site and then
-    applies the operator; oracle.dirac_sites does both per listed site, so a
-    quarter of the sites is a quarter of the work.  Returns (solves/s, seconds
-    of the sample, description)."""
+def oracle_d_sample(U, sample_frac):
+    """Times the oracle's D (one thread) at every (1/sample_frac)-th site of the
+    workload.  The oracle's full D computes the clover field at every site and
+    then applies the operator; oracle.dirac_sites does both per listed site,
+    so a fraction of the sites is that fraction of the work.  Returns (seconds
+    per full-lattice D, seconds of the sample, sites sampled)."""
     import oracle
     from paper_2503_16994_gb300 import inputs
     dims = tuple(WORKLOAD["lattice"])
     V = inputs.volume(dims)
     psi = inputs.spinor_field(dims, seed=2)
-    nsample = int(V * sample_frac)
-    sites = np.arange(0, V, int(round(1 / sample_frac)))[:nsample]
+    step = int(round(1 / sample_frac))
+    sites = np.arange(0, V, step)
     t0 = time.perf_counter()
     oracle.dirac_sites(dims, U, WORKLOAD["kappa"], WORKLOAD["csw"], psi, sites)
     dt = time.perf_counter() - t0
-    t_D = dt * V / len(sites)
-    solve_s = 2.0 * ORACLE_ITERS * t_D
-    desc = (f"oracle D (FP64, 1 thread) at {len(sites)} of {V} sites of the 32^3x64 workload in {dt:.2f} s "
-            f"-> {t_D:.1f} s per full-lattice D; one solve costed as 2 x {ORACLE_ITERS} D applications")
-    return 1.0 / solve_s, dt, desc
+    return dt * V / len(sites), dt, len(sites)
+
+
+def _oracle_sites_worker(args):
+    """Pool worker: the oracle's D at a slice of sites, fields in shared memory."""
+    from multiprocessing import shared_memory
+
+    import oracle
+    name_u, shape_u, name_p, shape_p, dims, kappa, csw, sites = args
+    su, sp = shared_memory.SharedMemory(name=name_u), shared_memory.SharedMemory(name=name_p)
+    try:
+        U = np.ndarray(shape_u, dtype=np.complex128, buffer=su.buf)
+        psi = np.ndarray(shape_p, dtype=np.complex128, buffer=sp.buf)
+        t0 = time.perf_counter()
+        oracle.dirac_sites(dims, U, kappa, csw, psi, sites)
+        dt = time.perf_counter() - t0
+        del U, psi
+    finally:
+        su.close()
+        sp.close()
+    return dt
+
+
+def oracle_d_all_cores(U, sample_frac, cores):
+    """The same sample split over `cores` oracle processes (spawned; the fields
+    shared, not copied).  Returns (seconds per full-lattice D, wall seconds)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    from paper_2503_16994_gb300 import inputs
+    dims = tuple(WORKLOAD["lattice"])
+    V = inputs.volume(dims)
+    psi = inputs.spinor_field(dims, seed=2)
+    sites = np.arange(0, V, int(round(1 / sample_frac)))
+    su = shared_memory.SharedMemory(create=True, size=U.nbytes)
+    sp = shared_memory.SharedMemory(create=True, size=psi.nbytes)
+    try:
+        np.ndarray(U.shape, dtype=np.complex128, buffer=su.buf)[...] = U
+        np.ndarray(psi.shape, dtype=np.complex128, buffer=sp.buf)[...] = psi
+        parts = np.array_split(sites, cores)
+        jobs = [(su.name, U.shape, sp.name, psi.shape, dims, WORKLOAD["kappa"], WORKLOAD["csw"], part)
+                for part in parts]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_sites_worker, [(j[0], j[1], j[2], j[3], j[4], j[5], j[6], j[7][:8]) for j in jobs])
+            t0 = time.perf_counter()
+            pool.map(_oracle_sites_worker, jobs)
+            wall = time.perf_counter() - t0
+    finally:
+        su.close()
+        su.unlink()
+        sp.close()
+        sp.unlink()
+    return wall * V / len(sites), wall
+
+
+def oracle_c1_solve():
+    """The oracle's full solve of config 1 as stated (4^4, eps 0.2, kappa
+    0.120, csw 1.0, one point source, CGNR to 1e-10), one thread."""
+    import oracle
+    from paper_2503_16994_gb300 import inputs
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, 0.2, seed=1)
+    b = inputs.point_source(dims, (0, 0, 0, 0), 0, 0)
+    t0 = time.perf_counter()
+    _, it, res, ok = oracle.cgnr(dims, U, 0.120, 1.0, b, tol=1e-10)
+    return {"ms": (time.perf_counter() - t0) * 1e3, "iters": it, "true_resid": res, "converged": ok}
+
+
+def cpu_baseline_measure(U):
+    """The oracle on the host cores: its D at an eighth of the workload's sites,
+    one thread and all cores, each costed as 2 x ORACLE_ITERS D applications
+    per solve (solves/s); plus the full config-1 solve, timed."""
+    cores = len(os.sched_getaffinity(0))
+    t_d1, dt1, n1 = oracle_d_sample(U, 1 / 8)
+    t_dn, wall = oracle_d_all_cores(U, 1 / 8, cores)
+    return {"value": 1.0 / (2.0 * ORACLE_ITERS * t_dn), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle D (FP64) at {n1} of the 32^3x64 sites on {cores} processes in {wall:.2f} s "
+                      f"-> {t_dn:.2f} s per full-lattice D; a solve costed as 2 x {ORACLE_ITERS} D applications",
+            "one_thread": {"value": 1.0 / (2.0 * ORACLE_ITERS * t_d1), "s_per_D": t_d1, "sample_s": dt1},
+            "c1_full_solve": oracle_c1_solve()}
 
 
 # ---------------------------------------------------------------------------
@@ -265,7 +369,7 @@ def dslash_measure(lqcd, lat, gid, dp, dims, legs=DSLASH_LEGS):
     return out
 
 
-def meson_measure(lqcd, lat, dims, repeat=5):
+def meson_measure(lqcd, dims, repeat=5):
     """Times lqcd_meson_contract for the 16 Clifford spin matrices on a
     12-column array of the workload's size (values do not change the cost).
     FP64 throughout: per site 256 terms of 9 complex conj-products and one
@@ -285,15 +389,19 @@ def meson_measure(lqcd, lat, dims, repeat=5):
     prop.real.normal_()
     prop.imag.normal_()
     c = torch.zeros((16, T), dtype=torch.complex128, device="cuda")
-    lqcd.meson_contract(lat, prop, 0, gam, corr=c)  # warm-up
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(repeat):
-        lqcd.meson_contract(lat, prop, 0, gam, corr=c)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / repeat
+    lat = lqcd.lattice_create(dims)
+    try:
+        lqcd.meson_contract(lat, prop, 0, gam, corr=c)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(repeat):
+            lqcd.meson_contract(lat, prop, 0, gam, corr=c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / repeat
+    finally:
+        lqcd.lattice_destroy(lat)
     del prop
     torch.cuda.empty_cache()
     flops = 256 * 80.0 * V
@@ -318,6 +426,127 @@ def run_dslash_only(args):
     res = dslash_measure(lqcd, lat, gid, dp, dims, legs)
     lqcd.lattice_destroy(lat)
     print(json.dumps({"dslash": res, "lattice": list(dims), "tuning": lqcd.tune_report()}))
+
+
+# ---------------------------------------------------------------------------
+# small configurations against oracle-solved golden propagators
+# ---------------------------------------------------------------------------
+GOLDEN = {"c1": os.path.join(ROOT, "tests", "golden", "pion_4c4_seed1.json"),
+          "c2": os.path.join(ROOT, "tests", "golden", "pion_16c32_seed1.json")}
+
+
+def golden_errors(doc, corr, prop=None):
+    """Largest relative error of C(t) per slice, and of the propagator at the
+    golden's sampled sites (max |S - S_oracle| / max |S_oracle| per column),
+    against the oracle-solved golden (FP64 CPU oracle, CGNR to 1e-13)."""
+    ref = np.asarray(doc["corr"])
+    out = {"corr_rel_max": float(np.max(np.abs(np.asarray(corr) - ref) / np.abs(ref)))}
+    if prop is not None:
+        vals = np.asarray(doc["samples"]["values"])  # [12][site][12][2]
+        want = vals[..., 0] + 1j * vals[..., 1]
+        errs = []
+        for j in range(12):
+            got = np.array([prop[j, s[3], s[2], s[1], s[0]].reshape(12) for s in doc["samples"]["sites"]])
+            errs.append(np.max(np.abs(got - want[j])) / np.max(np.abs(want[j])))
+        out["prop_sites_rel_max"] = float(max(errs))
+    return out
+
+
+def small_config_measure(lqcd, name, precisions, reps):
+    """A 12-column propagator per precision on a golden's configuration: solves/s
+    (device pointers, inputs resident) and the errors against the golden."""
+    import torch
+    from paper_2503_16994_gb300 import inputs
+    path = GOLDEN[name]
+    if not os.path.exists(path):
+        return {"skipped": f"golden file {os.path.basename(path)} missing"}
+    doc = json.load(open(path))
+    c = doc["config"]
+    dims = tuple(c["dims"])
+    U = inputs.gauge_field(dims, c["eps"], seed=c["seed"], workers=None)
+    lat = lqcd.lattice_create(dims)
+    out = {"lattice": list(dims), "kappa": c["kappa"], "csw": c["csw"], "eps": c["eps"]}
+    try:
+        gid = lqcd.gauge_upload(lat, U)
+        dp = lqcd.dirac_params(c["kappa"], c["csw"])
+        V = int(np.prod(dims))
+        corr = torch.zeros(dims[3], dtype=torch.float64, device="cuda")
+        prop = torch.zeros(12 * V * 12, dtype=torch.complex128, device="cuda")
+        stream = torch.cuda.current_stream()
+        for prec in precisions:
+            sp = lqcd.solver_params(tol=1e-10, maxiter=20000, precision=prec)
+            lqcd.pion_corr(lat, gid, dp, sp, tuple(c["src"]), device_out=(corr, prop), stream=stream)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                _, _, infos, rc = lqcd.pion_corr(lat, gid, dp, sp, tuple(c["src"]), device_out=(corr, prop),
+                                                 stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            pr = prop.cpu().numpy().reshape(12, dims[3], dims[2], dims[1], dims[0], 4, 3)
+            out[prec] = {"solves_per_s": 12 / (ms / 1e3), "ms_per_propagator": ms, "converged": rc == lqcd.OK,
+                         "iters_max": max(i["iters_inner"] for i in infos),
+                         "true_resid_max": max(i["true_resid"] for i in infos),
+                         **golden_errors(doc, corr.cpu().numpy(), pr)}
+    finally:
+        lqcd.lattice_destroy(lat)
+    if "fp64" in out and "fp32" in out:
+        out["mixed_fp32_vs_fp64"] = out["fp32"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    if "fp64" in out and "fp16" in out:
+        out["mixed_fp16_vs_fp64"] = out["fp16"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    out["golden"] = os.path.relpath(path, ROOT)
+    return out
+
+
+def compact_small(leg):
+    """Solves/s and errors against the golden per precision, for the JSON line."""
+    if not leg or "skipped" in leg:
+        return leg
+    out = {p: [leg[p]["solves_per_s"], leg[p]["corr_rel_max"], leg[p]["prop_sites_rel_max"]]
+           for p in ("fp64", "fp32", "fp16") if p in leg}
+    out["cols"] = "solves/s, C(t) err, prop err vs oracle golden"
+    if "single_source" in leg:
+        out["fp64_1rhs_ms"] = leg["single_source"]["ms_per_solve"]
+    return out
+
+
+def c1_latency(lqcd, reps=20):
+    """Config 1 as stated: one point source (spin 0, colour 0) at the origin of
+    the 4^4 lattice, plain FP64 CG to 1e-10 (lqcd_cg_solve, device pointers):
+    the latency of one solve, and its error against the golden's column 0."""
+    import torch
+    from paper_2503_16994_gb300 import inputs
+    path = GOLDEN["c1"]
+    if not os.path.exists(path):
+        return {"skipped": "golden file missing"}
+    doc = json.load(open(path))
+    c = doc["config"]
+    dims = tuple(c["dims"])
+    U = inputs.gauge_field(dims, c["eps"], seed=c["seed"], workers=None)
+    b = torch.from_numpy(inputs.point_source(dims, tuple(c["src"]), 0, 0)).cuda()
+    x = torch.empty_like(b)
+    lat = lqcd.lattice_create(dims)
+    try:
+        gid = lqcd.gauge_upload(lat, U)
+        dp = lqcd.dirac_params(c["kappa"], c["csw"])
+        sp = lqcd.solver_params(tol=1e-10, maxiter=20000, precision="fp64")
+        lqcd.cg_solve(lat, gid, dp, sp, b, x=x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, infos, rc = lqcd.cg_solve(lat, gid, dp, sp, b, x=x)
+        dt = (time.perf_counter() - t0) / reps
+    finally:
+        lqcd.lattice_destroy(lat)
+    xs = x.cpu().numpy()
+    vals = np.asarray(doc["samples"]["values"][0])
+    want = vals[..., 0] + 1j * vals[..., 1]
+    got = np.array([xs[s[3], s[2], s[1], s[0]].reshape(12) for s in doc["samples"]["sites"]])
+    return {"lattice": list(dims), "precision": "fp64", "ms_per_solve": dt * 1e3, "iters": infos[0]["iters_inner"],
+            "true_resid": infos[0]["true_resid"], "converged": rc == lqcd.OK,
+            "x_sites_rel_err": float(np.max(np.abs(got - want)) / np.max(np.abs(want)))}
 
 
 # ---------------------------------------------------------------------------
@@ -429,7 +658,7 @@ def batch_measure(lqcd, per_size=None):
     return {"propagators": len(jobs), "converged": rc == lqcd.OK, "batched_solves_per_s": n / tb,
             "sequential_mixed_solves_per_s": n / tseq, "sequential_fp64_solves_per_s_est": n / t64,
             "batched_vs_sequential_mixed": tseq / tb, "batched_vs_sequential_fp64_est": t64 / tb,
-            "batched_s": tb, "tuning": [t for t in lqcd.tune_report() if t["nrhs"] == 12],
+            "batched_s": tb,
             "workload": "16 each of 8^3x16, 12^3x24, 16^3x32, 24^3x48; eps 0.3; kappa U[0.120,0.132]; csw 1.5; "
                         "12 RHS FP16 mixed; tol 1e-10; one graph per chunk of 8 iterations"}
 
@@ -476,9 +705,10 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
+    # timed region: launches are counted, not bracketed by events
     clocks = ClockSampler(local)
     clocks.start()
-    lqcd.profile_reset(timing=True)
+    lqcd.profile_reset(timing=False)
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -491,12 +721,25 @@ def run_ours(args):
     torch.cuda.cudart().cudaProfilerStop()
     barrier(world)
     ms = e0.elapsed_time(e1)
-    prof = lqcd.profile_read()
     clk = clocks.stop()
+    launches = int(sum(v["launches"] for v in lqcd.profile_read().values()))
     ms_max = max_over_ranks(ms, world)
     value = nrhs * args.steps * world / (ms_max / 1e3)
+    infos_timed = infos_last
 
-    # roofline of the dominant kernel family: the FP16 hopping kernels
+    # kernel split and roofline: the same step again with every launch
+    # bracketed by CUDA events on its own stream (after the timed region)
+    psteps = max(1, min(args.steps, args.profile_steps))
+    lqcd.profile_reset(timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(psteps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = e0.elapsed_time(e1)
+    prof = lqcd.profile_read()
+
     hop = {k: v for k, v in prof.items() if k.startswith("hop_f16")}
     hop_ms = sum(v["timed_ms"] for v in hop.values())
     hop_bytes = sum(v["timed_bytes"] for v in hop.values())
@@ -504,18 +747,26 @@ def run_ours(args):
     total_ms = sum(v["timed_ms"] for v in prof.values())
     achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
     sites_h = inputs.volume(dims) // 2
-    hop_flops = sum(v["timed_launches"] * sites_h * nrhs * HOP_FLOPS[k] for k, v in hop.items() if k in HOP_FLOPS)
+    # flops over the right-hand sides a launch worked on (bytes / per-RHS bytes)
+    hop_flops = 0.0
+    for k, v in hop.items():
+        if k in HOP_FLOPS and v["timed_launches"]:
+            per_rhs = HOP_BYTES_PER_RHS[k]
+            shared = HOP_BYTES_SHARED[k]
+            rhs_sites = (v["timed_bytes"] - v["timed_launches"] * sites_h * shared) / per_rhs
+            hop_flops += rhs_sites * HOP_FLOPS[k]
     alu_achieved = hop_flops / (hop_ms / 1e3) / 1e12 if hop_ms > 0 else 0.0
+    fp32_peak, sms = fp32_peak_tflops()
     peak, peak_kind = hbm_peak()
-    launches = int(sum(v["launches"] for v in prof.values()))
     traffic = None
     if kernel_digest() == HOP_TRAFFIC["digest"] and hop_launches:
-        sites = inputs.volume(dims) // 2
-        tb = sum(v["timed_launches"] * HOP_TRAFFIC[k] * sites for k, v in hop.items() if k in HOP_TRAFFIC)
+        tb = sum(v["timed_launches"] * HOP_TRAFFIC[k] * sites_h for k, v in hop.items() if k in HOP_TRAFFIC)
         traffic = tb / hop_launches
     per_kernel = {k: {"launches": v["launches"], "ms": round(v["timed_ms"], 3),
                       "GB/s": round(v["timed_bytes"] / max(v["timed_ms"], 1e-9) / 1e6, 1)}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["timed_ms"])}
+    shares = {k: round(v["timed_ms"] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["timed_ms"])
+              if total_ms and v["timed_ms"] / total_ms >= 0.01}
 
     # e2e through the host-pointer API (pinned host buffers)
     e2e = None
@@ -541,7 +792,7 @@ def run_ours(args):
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ke = max(1, args.steps // 2)
+        ke = max(1, min(args.steps // 2, 5))
         for _ in range(ke):
             e2e_step()
         torch.cuda.synchronize()
@@ -565,45 +816,71 @@ def run_ours(args):
                 "true_resid_max": max(i["true_resid"] for i in infos64)}
 
     dslash = None if args.no_dslash else dslash_measure(lqcd, lat, gid, dp, dims)
-    meson = None if (args.no_meson or rank != 0) else meson_measure(lqcd, lat, dims)
-    serving = None if (args.serve_requests <= 0 or rank != 0) else serving_measure(lqcd, args.serve_requests)
+    lqcd.lattice_destroy(lat)
+    lat = None
+    small = rank == 0 and not args.no_small
+    c2 = small_config_measure(lqcd, "c2", ["fp64", "fp32", "fp16"], reps=2) if small else None
+    c1 = None
+    if small:
+        c1 = small_config_measure(lqcd, "c1", ["fp64", "fp16"], reps=5)
+        c1["single_source"] = c1_latency(lqcd)
+    meson = None if (args.no_meson or rank != 0) else meson_measure(lqcd, dims)
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        hi = serving_measure(lqcd, args.serve_requests)
+        # a second stream at offered load ~0.7 from the measured mean service time
+        low_rate = 0.7 * SERVE["slots"] / max(hi["mean_service_s"], 1e-3)
+        lo = serving_measure(lqcd, max(8, args.serve_requests // 2), rate=low_rate)
+        serving = [hi, lo]
     batch = None if (args.no_batch or rank != 0) else batch_measure(lqcd)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, desc = cpu_baseline_measure(U)
-        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = cpu_baseline_measure(U)
 
     if rank == 0:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "hop_f16_hopclov+selfclov",
+                "bytes_per_launch": hop_bytes / hop_launches if hop_launches else None,
+                "peak_source": f"{peak_kind} hbm_gbs", "frac_8TBs": achieved / NOMINAL_HBM_GBS,
+                "share": hop_ms / total_ms if total_ms else None, "launches": hop_launches,
+                # the same kernels against the FP32 CUDA-core roof (SM count from the device)
+                "alu": {"achieved": alu_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": alu_achieved / fp32_peak}}
         out = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**WORKLOAD, "parallelism": f"replicas x{world} (independent propagators)",
-                       "storage": "spinors FP16 + per-site FP32 scale, links FP16 recon-12, clover FP16; "
-                                  "FP32 arithmetic; FP64 reliable updates and final residual"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "hop_f16_* (hopclov + selfclov)",
-                         "traffic_source": "ncu capture at 24^3x48 scaled by sites (profiles/)",
-                         "algorithmic_bytes_per_launch": hop_bytes / hop_launches if hop_launches else None,
-                         "peak_source": f"{peak_kind} hbm_gbs", "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS,
-                         "launches": hop_launches, "share_of_device_time": hop_ms / total_ms if total_ms else None,
-                         # the same kernels against the FP32 CUDA-core roof: at 12 RHS they sit at the
-                         # ridge (hopclov slightly above it, selfclov slightly below)
-                         "alu": {"achieved": alu_achieved, "peak": NOMINAL_FP32_TFLOPS, "unit": "TFLOP/s",
-                                 "frac": alu_achieved / NOMINAL_FP32_TFLOPS,
-                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                                 "flops_per_site_rhs": HOP_FLOPS}},
-            "dslash": dslash, "meson": meson, "serving": serving, "batched": batch, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
-            "fp64_gpu": fp64, "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
-            "iters": {"inner_max": max(i["iters_inner"] for i in infos_last),
-                      "outer_max": max(i["iters_outer"] for i in infos_last),
-                      "true_resid_max": max(i["true_resid"] for i in infos_last)},
-            "kernels": per_kernel,
-            "tuning": lqcd.tune_report(),
+            "config": bench_config(world),
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "iters": {"inner_max": max(i["iters_inner"] for i in infos_timed),
+                      "outer_max": max(i["iters_outer"] for i in infos_timed),
+                      "true_resid_max": max(i["true_resid"] for i in infos_timed)},
+            "fp64_gpu": None if fp64 is None else {k: fp64[k] for k in ("solves_per_s", "iters_max")},
+            "mixed_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
+            "kernel_share": dict(list(shares.items())[:6]),
+            "dslash": None if not dslash else {k: [v["GB/s"], v["frac_of_measured"], v["us_per_hop"]]
+                                               for k, v in dslash.items()},
+            "c2": compact_small(c2), "c1": compact_small(c1),
+            "serving": None if not serving else [{k: sv[k] for k in ("rate_per_s", "requests", "p50_s", "p99_s",
+                                                                        "offered_load_rho", "solves_per_s")}
+                                                 for sv in serving],
+            "batched": None if not batch else {k: batch[k] for k in ("batched_solves_per_s",
+                                                                     "batched_vs_sequential_mixed",
+                                                                     "batched_vs_sequential_fp64_est")},
+            "meson_ms": None if not meson else meson["ms"],
         }
-        print(json.dumps(out))
-    lqcd.lattice_destroy(lat)
+        # the JSON line is kept short (rounded, summaries only); the full legs go to stderr
+        print(json.dumps({"bench_details": {"kernels": per_kernel, "tuning": lqcd.tune_report(), "dslash": dslash,
+                                            "c2": c2, "c1": c1, "serving": serving, "batched": batch, "meson": meson,
+                                            "cpu_baseline": cpu, "fp64_gpu": fp64, "roofline_timed_over":
+                                            f"{psteps} profiled steps after the timed region",
+                                            "ms_per_step_profiled": ms_prof / psteps}}), file=sys.stderr)
+        print(json.dumps(r4(out)))
+        sys.stdout.flush()
+    if lat is not None:
+        lqcd.lattice_destroy(lat)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -622,20 +899,22 @@ def run_reference(args):
     oracle.build()
     dims = tuple(WORKLOAD["lattice"])
     U = inputs.gauge_field(dims, WORKLOAD["eps"], seed=WORKLOAD["seed"], workers=None)
-    # a step is the oracle's D on a sixteenth of the sites (about 2 s)
+    # a step is the oracle's D on a sixteenth of the sites (about 2 s), costed per solve
     for _ in range(args.warmup):
-        cpu_baseline_measure(U, sample_frac=1 / 16)
+        oracle_d_sample(U, 1 / 16)
     vals, secs = [], 0.0
     desc = ""
     for _ in range(args.steps):
-        v, dt, desc = cpu_baseline_measure(U, sample_frac=1 / 16)
-        vals.append(v)
+        t_d, dt, n = oracle_d_sample(U, 1 / 16)
+        vals.append(1.0 / (2.0 * ORACLE_ITERS * t_d))
         secs += dt
+        desc = (f"oracle D (FP64, 1 thread) at {n} of the 32^3x64 sites per step -> {t_d:.1f} s per "
+                f"full-lattice D; a solve costed as 2 x {ORACLE_ITERS} D applications")
     value = float(np.median(vals))
     out = {"metric": METRIC, "impl": "reference", "value": value, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {**WORKLOAD, "parallelism": "1 host thread"},
+           "config": bench_config(world),
            "cpu_baseline": {"value": value, "unit": "solves/s", "kind": "oracle", "cores": 1, "sample": desc},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -653,6 +932,9 @@ def main():
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-meson", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the 16^3x32 and 4^4 legs against the goldens")
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="steps re-run with every launch timed, for the kernel split and the roofline")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
     ap.add_argument("--dslash-only", action="store_true", help="time only the Dslash on --lattice")
     ap.add_argument("--lattice", default="32,32,32,64")

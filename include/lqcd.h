@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define LQCD_ABI_VERSION 1
+#define LQCD_ABI_VERSION 2
 
 /* status codes */
 enum {
@@ -78,19 +78,39 @@ enum {
     LQCD_GUESS = 4        /* lqcd_cg_solve: x holds an initial guess on input (resume, warm start) */
 };
 
+/* boundary conditions in time (SpaceParm's BC of Sec. 2.1) */
+enum {
+    LQCD_BC_PERIODIC = 0, /* every direction closes on itself, the hops across carry theta_mu */
+    LQCD_BC_OPEN = 1      /* open in time: no link from the slice x_t = T - 1 to x_t = 0 (hops and clover
+                             leaves across vanish, theta_t plays no part); the slices x_t = 0 and T - 1 get
+                             the boundary improvement term 2 kappa (cF - 1) */
+};
+
 typedef struct lqcd_lattice_s *lqcd_lattice; /* opaque; owns all device memory it allocates */
 typedef struct lqcd_server_s *lqcd_server;   /* opaque serving loop */
 
 /* DiracParam of Sec. 3.3 (kappa instead of m0).  theta: the four boundary
- * phase factors (|theta_mu| = 1), re and im parts.  mu (twisted mass, mass
- * units; the kappa-normalised site term would gain 2 i kappa mu g5) must be
- * 0 in this version: any call given mu != 0 returns LQCD_ENOTIMPL. */
+ * phase factors (|theta_mu| = 1), re and im parts.  mu: twisted mass in mass
+ * units, one flavour: the kappa-normalised site term gains 2 i kappa mu g5
+ * (the paper's D_w gains i mu g5 and D = 2 kappa D_w), so
+ *   D(mu) = D + 2 i kappa mu g5,   D(mu)^dag = g5 D(-mu) g5;
+ * every call takes it (0: the Wilson-clover operator).  Per chirality block
+ * A_s (s = +1 spins 0-1, -1 spins 2-3) the site term A_s + i s tau, tau =
+ * 2 kappa mu, is inverted as B_s - i s tau C_s with C_s = (A_s^2 + tau^2)^-1
+ * and B_s = A_s C_s.  Solves at mu != 0 run on the generic (untuned) hopping
+ * kernel in every storage format.  mu must be finite (LQCD_EINVAL).
+ * bc: LQCD_BC_PERIODIC (0) or LQCD_BC_OPEN; cF: the boundary improvement
+ * coefficient of DiracParam (Sec. 3.3), used with LQCD_BC_OPEN only (the T
+ * slices of the lattice are all dynamical; the paper's iL[4] - 1 effective
+ * slices are this T).  A zero-initialised struct is the periodic operator. */
 typedef struct {
     double kappa;
     double csw;
     double theta_re[4];
     double theta_im[4];
     double mu;
+    double cF;
+    int bc;
 } lqcd_dirac_params;
 
 /* tol: stop when the true relative residual |b - D x|_2 / |b|_2 of the full
@@ -156,7 +176,7 @@ int lqcd_gauge_free(lqcd_lattice lat, int gauge_id);
  * (Csw! of Sec. 3.3).  psi_in, psi_out: 24 V doubles each, host layout; host
  * memory, or device memory with LQCD_DEVICE_PTRS.  psi_in and psi_out must
  * not overlap.
- * Errors: LQCD_EINVAL (null, unknown id, mu != 0), LQCD_ENOMEM, LQCD_ECUDA. */
+ * Errors: LQCD_EINVAL (null, unknown id, non-finite parameters), LQCD_ENOMEM, LQCD_ECUDA. */
 int lqcd_dirac_apply(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp,
                      const double *psi_in, double *psi_out, int flags, void *stream);
 
@@ -263,6 +283,50 @@ int lqcd_pion_contract(lqcd_lattice lat, const double *prop, int src_t, double *
 #define LQCD_MESON_MAX_GAMMAS 64
 int lqcd_meson_contract(lqcd_lattice lat, const double *prop, int src_t, const double *gammas, int ng, double *corr,
                         int flags, void *stream);
+
+/* Boundary-to-bulk correlators (Sec. 3.3: the propagators from the boundary
+ * that give f_P and f_A), on the operator of dp (meant for LQCD_BC_OPEN):
+ * the six sources W_j(y) = delta_{y_t, 0} P+ e_j, j = 3 s + c with spin s in
+ * {0, 1} and colour c, P+ = (1 + g_t) / 2, on every site of the slice y_t = 0
+ * (zero spatial momentum; P+ e_{j+6} = -P+ e_j adds nothing), are solved as
+ * one batch, H_j = D^-1 W_j, and per slice
+ *   fP[x_t] = sum_xvec sum_j |H_j(x)|^2,
+ *   fA[x_t] = - sum_xvec sum_j Re <H_j(x), g_t H_j(x)>.
+ * fP, fA: T doubles each; H: NULL or 6 * 24 V doubles receiving the columns;
+ * all host memory, or device memory with LQCD_DEVICE_PTRS.  info: 6 entries
+ * or NULL.  Returns as lqcd_cg_solve. */
+int lqcd_boundary_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, const lqcd_solver_params *sp,
+                       double *fP, double *fA, double *H, lqcd_solve_info *info, int flags, void *stream);
+
+/* ---------------- gauge observables and the Wilson flow (Sec. 3.2) ---- */
+
+/* Wilson flow of a resident gauge field, in place (flw with the wfl_rk3
+ * scheme of Sec. 3.2): nsteps steps of size eps of the third-order
+ * Runge-Kutta integrator of Luescher (JHEP 2010, the reference the paper
+ * cites), flow time t = nsteps eps:
+ *   W1 = exp(Z0/4) W0,  W2 = exp(8 Z1/9 - 17 Z0/36) W1,
+ *   V(t + eps) = exp(3 Z2/4 - 8 Z1/9 + 17 Z0/36) W2,   Z_i = eps Z(W_i),
+ * Z_mu(x) = -(1/2)(Omega - Omega^dag) + (1/6) tr(Omega - Omega^dag), Omega =
+ * U_mu(x) times the sum of its six staples (the force of the Wilson action
+ * over oriented plaquettes); periodic in every direction; FP64 on the GPU.
+ * The FP32/FP16 copies are rebuilt and the cached clover fields dropped.
+ * Errors: LQCD_EINVAL (unknown id, eps <= 0, nsteps < 0), LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_gauge_flow(lqcd_lattice lat, int gauge_id, double eps, int nsteps, void *stream);
+
+/* Gauge observables of a resident field (plaquette, Eoft_plaq, Eoft_clover
+ * and Qtop of Sec. 3.2), FP64, host outputs (any may be NULL):
+ *   *plaq    = (1 / 6V) sum_x sum_{mu<nu} Re tr U_p(x) / 3   (1 for the unit field),
+ *   Eplaq[t] = sum_xvec 2 sum_{mu<nu} Re tr (1 - U_p(x)),
+ *   Eclov[t] = sum_xvec - sum_{mu<nu} tr F_{mu nu}(x)^2,
+ *   Q[t]     = sum_xvec -(1 / 32 pi^2) eps_{mu nu rho sigma} tr F_{mu nu}(x) F_{rho sigma}(x),
+ * per time slice t (T values each), F the antihermitian clover field of
+ * lqcd_dirac_apply; divide by L^3 for the densities. */
+int lqcd_gauge_observables(lqcd_lattice lat, int gauge_id, double *plaq, double *Eplaq, double *Eclov, double *Q,
+                           void *stream);
+
+/* The resident FP64 links in the host layout of lqcd_gauge_upload (72 V
+ * doubles; host memory, or device memory with LQCD_DEVICE_PTRS). */
+int lqcd_gauge_download(lqcd_lattice lat, int gauge_id, double *U, int flags, void *stream);
 
 /* ---------------- launch accounting and timing ------------------------- */
 

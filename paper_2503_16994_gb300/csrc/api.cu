@@ -40,7 +40,9 @@ static int check_params(const lqcd_dirac_params *dp)
     if (!dp) return fail(LQCD_EINVAL, "null dirac params");
     if (!(dp->kappa >= 0.0) || !std::isfinite(dp->kappa)) return fail(LQCD_EINVAL, "kappa must be finite and >= 0");
     if (!std::isfinite(dp->csw)) return fail(LQCD_EINVAL, "csw must be finite");
-    if (dp->mu != 0.0) return fail(LQCD_ENOTIMPL, "twisted mass mu != 0 is not supported");
+    if (!std::isfinite(dp->mu)) return fail(LQCD_EINVAL, "mu must be finite");
+    if (dp->bc != LQCD_BC_PERIODIC && dp->bc != LQCD_BC_OPEN) return fail(LQCD_EINVAL, "unknown boundary condition");
+    if (dp->bc == LQCD_BC_OPEN && !std::isfinite(dp->cF)) return fail(LQCD_EINVAL, "cF must be finite");
     for (int m = 0; m < 4; ++m)
         if (!std::isfinite(dp->theta_re[m]) || !std::isfinite(dp->theta_im[m]))
             return fail(LQCD_EINVAL, "theta must be finite");
@@ -149,6 +151,73 @@ int lqcd_gauge_free(lqcd_lattice lat, int gauge_id)
     if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
     LQCD_CUDA(cudaDeviceSynchronize());
     lat->gauges.erase(it);
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_gauge_flow(lqcd_lattice lat, int gauge_id, double eps, int nsteps, void *stream)
+{
+    if (!lat) return fail(LQCD_EINVAL, "null lattice");
+    if (!(eps > 0.0) || !std::isfinite(eps) || nsteps < 0) return fail(LQCD_EINVAL, "eps must be > 0, nsteps >= 0");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    gauge_flow(lat, *it->second, eps, nsteps, static_cast<cudaStream_t>(stream));
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_gauge_observables(lqcd_lattice lat, int gauge_id, double *plaq, double *Eplaq, double *Eclov, double *Q,
+                           void *stream)
+{
+    if (!lat) return fail(LQCD_EINVAL, "null lattice");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int T = lat->dims[3];
+    DevBuf out;
+    out.ensure(sizeof(double) * 4 * T);
+    gauge_observables(lat, *it->second, out.as<double>(), st);
+    std::vector<double> h(4 * T);
+    LQCD_CUDA(cudaMemcpyAsync(h.data(), out.p, sizeof(double) * 4 * T, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    if (plaq) {
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += h[t];
+        *plaq = s / (6.0 * double(lat->V));
+    }
+    for (int t = 0; t < T; ++t) {
+        if (Eplaq) Eplaq[t] = h[T + t];
+        if (Eclov) Eclov[t] = h[2 * T + t];
+        if (Q) Q[t] = h[3 * T + t];
+    }
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_gauge_download(lqcd_lattice lat, int gauge_id, double *U, int flags, void *stream)
+{
+    if (!lat || !U) return fail(LQCD_EINVAL, "null argument");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(double) * 72 * (size_t)lat->V;
+    double *Ud = U;
+    if (!(flags & LQCD_DEVICE_PTRS)) {
+        lat->staging.ensure(bytes);
+        Ud = lat->staging.as<double>();
+    }
+    gauge_download(lat, *it->second, Ud, st);
+    if (!(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(U, Ud, bytes, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
     return LQCD_OK;
     API_CATCH
 }
@@ -272,6 +341,46 @@ int lqcd_pion_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, 
         if (prop) LQCD_CUDA(cudaMemcpyAsync(prop, prop_d, pbytes, cudaMemcpyDeviceToHost, st));
         LQCD_CUDA(cudaStreamSynchronize(st));
     }
+    if (failed) return fail(LQCD_ENOCONV, std::to_string(failed) + " column(s) did not converge");
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_boundary_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, const lqcd_solver_params *sp,
+                       double *fP, double *fA, double *H, lqcd_solve_info *info, int flags, void *stream)
+{
+    if (!lat || !fP || !fA) return fail(LQCD_EINVAL, "null argument");
+    if (int rc = check_params(dp)) return rc;
+    if (int rc = check_solver(sp)) return rc;
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int T = lat->dims[3];
+    const size_t cbytes = sizeof(double) * 24 * (size_t)lat->V * 6;
+    lat->staging.ensure(cbytes);  // the six wall sources
+    double *H_d = H;
+    if (!(flags & LQCD_DEVICE_PTRS) || !H) {
+        lat->staging2.ensure(cbytes);
+        H_d = lat->staging2.as<double>();
+    }
+    DevBuf fbuf;  // fP then fA on the device
+    fbuf.ensure(sizeof(double) * 2 * T);
+    double *f_d = fbuf.as<double>();
+    wall_sources_p_plus(lat, lat->staging.as<double>(), st);
+    int failed = solve(lat, gauge_id, *dp, *sp, lat->staging.as<const double>(), H_d, nullptr, 6, info, nullptr, st);
+    const long nchunk = (lat->V / T + kBlock - 1) / kBlock;
+    lat->red_partial.ensure(sizeof(double) * 2 * (size_t)T * nchunk);
+    if (lat->red_counter.bytes < sizeof(unsigned) * (size_t)std::max(2 * T, 4096)) {
+        lat->red_counter.ensure(sizeof(unsigned) * (size_t)std::max(2 * T, 4096));
+        LQCD_CUDA(cudaMemsetAsync(lat->red_counter.p, 0, lat->red_counter.bytes, st));
+    }
+    boundary_contract(lat, H_d, f_d, f_d + T, lat->red_partial.as<double>(), lat->red_counter.as<unsigned>(), st);
+    const cudaMemcpyKind k = (flags & LQCD_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    LQCD_CUDA(cudaMemcpyAsync(fP, f_d, sizeof(double) * T, k, st));
+    LQCD_CUDA(cudaMemcpyAsync(fA, f_d + T, sizeof(double) * T, k, st));
+    if (H && !(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(H, H_d, cbytes, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
     if (failed) return fail(LQCD_ENOCONV, std::to_string(failed) + " column(s) did not converge");
     return LQCD_OK;
     API_CATCH

@@ -94,11 +94,11 @@ void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, Spin
     LQCD_CHECK_LAUNCH();
 }
 
-template <class W>
-void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> w, SpinorField<W> r, cudaStream_t st)
+template <class W, class WI>
+void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<WI> w, SpinorField<W> r, cudaStream_t st)
 {
-    ProfScope prof("cg_r_replace", double(v.vh) * nact(v) * (2.0 * 192.0 + spinor_bytes<W>()), st);
-    cg_r_replace<W><<<grid_of(v), kBlock, 0, st>>>(v, bhat, w, r);
+    ProfScope prof("cg_r_replace", double(v.vh) * nact(v) * (192.0 + spinor_bytes<WI>() + spinor_bytes<W>()), st);
+    cg_r_replace<W, WI><<<grid_of(v), kBlock, 0, st>>>(v, bhat, w, r);
     LQCD_CHECK_LAUNCH();
 }
 
@@ -111,10 +111,12 @@ void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st)
 
 template <class S, class C>
 void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
-                         cudaStream_t st)
+                         cudaStream_t st, double tau, CloverField<C> cl2)
 {
-    ProfScope prof("clover_apply", double(vh) * (nrhs * 2.0 * spinor_bytes<S>() + clover_bytes<C>()), st);
-    clover_apply_kernel<S, C><<<unsigned(ntiles_of(vh) * nrhs), kBlock, 0, st>>>(int(vh), nrhs, parity, cl, in, out);
+    ProfScope prof("clover_apply",
+                   double(vh) * (nrhs * 2.0 * spinor_bytes<S>() + (tau != 0.0 ? 2.0 : 1.0) * clover_bytes<C>()), st);
+    clover_apply_kernel<S, C>
+        <<<unsigned(ntiles_of(vh) * nrhs), kBlock, 0, st>>>(int(vh), nrhs, parity, cl, in, out, tau, cl2);
     LQCD_CHECK_LAUNCH();
 }
 
@@ -142,13 +144,17 @@ template void launch_p_update<F32>(const VecArgs &, const RhsState *, SpinorFiel
 template void launch_p_update<F16>(const VecArgs &, const RhsState *, SpinorField<F16>, SpinorField<F16>, cudaStream_t);
 template void launch_x_update<F64>(const VecArgs &, const RhsState *, SpinorField<F64>, SpinorField<F64>, cudaStream_t);
 template void launch_x_update<F32>(const VecArgs &, const RhsState *, SpinorField<F32>, SpinorField<F64>, cudaStream_t);
-template void launch_r_replace<F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F64>,
-                                    cudaStream_t);
-template void launch_r_replace<F32>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F32>,
-                                    cudaStream_t);
-template void launch_r_replace<F16>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F16>,
-                                    cudaStream_t);
+template void launch_r_replace<F64, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F64>,
+                                         cudaStream_t);
+template void launch_r_replace<F32, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F32>,
+                                         cudaStream_t);
+template void launch_r_replace<F16, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F16>,
+                                         cudaStream_t);
+template void launch_r_replace<F32, F32>(const VecArgs &, SpinorField<F64>, SpinorField<F32>, SpinorField<F32>,
+                                         cudaStream_t);
+template void launch_r_replace<F16, F32>(const VecArgs &, SpinorField<F64>, SpinorField<F32>, SpinorField<F16>,
+                                         cudaStream_t);
 template void launch_clover_apply<F64, F64>(long, int, int, CloverField<F64>, SpinorField<F64>, SpinorField<F64>,
-                                            cudaStream_t);
+                                            cudaStream_t, double, CloverField<F64>);
 
 }  // namespace lqcd

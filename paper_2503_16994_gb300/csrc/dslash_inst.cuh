@@ -78,8 +78,8 @@ static void hopq_dispatch(const FastHop<S> &f, int pf, int mode, bool dag, bool 
 // directions issued before their arithmetic (FP16/FP32 only);
 // nr == 12, 13: as nr == 0 with the words of 2 or 3 directions ahead staged
 // in shared memory by cp.async (FP16 only);
-// nr == 20, 21: the tile kernel, gpb = pairs (warps) per block, 21 with one
-// direction of loads ahead (FP16 only)
+// nr == 20, 21: the tile kernel, gpb = pairs (warps) per block, spinor words
+// staged one (20) or two (21) directions ahead (FP16 only)
 constexpr bool is_tile_shape(int nr) { return nr == 20 || nr == 21; }
 
 template <class S>
@@ -188,14 +188,6 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
                 cand.push_back(HopShape{12, gpb, 4, 1});
                 cand.push_back(HopShape{13, gpb, 3, 1});
             }
-        // tile kernel: all pairs of a tile in one block (up to 6 warps), or half of them
-        if (ngr >= 3) {
-            const int full = std::min(ngr, kTileMaxPairs);
-            for (int npw : {full, (full % 2 == 0 && full >= 4) ? full / 2 : 0})
-                if (npw > 0)
-                    for (int nr : {20, 21})
-                        for (int minb : {2, 3}) cand.push_back(HopShape{nr, npw, minb, 1});
-        }
     }
     if (!std::is_same<S, F64>::value)
         for (int pf : {2, 4, 8})
@@ -203,6 +195,10 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
                 if (gpb <= f.nrhs && (gpb == 1 || f.nrhs % gpb == 0)) cand.push_back(HopShape{-pf, gpb, 1, 1});
     HopShape best{1, 1, 1, 1};
     float best_ms = 1e30f;
+    // candidates are timed on every RHS (the caller's gate may be partial;
+    // the outputs of the fast kernels are scratch fields the launch that
+    // follows overwrites)
+    f.gate_st = nullptr;
     cudaEvent_t e0, e1;
     LQCD_CUDA(cudaEventCreate(&e0));
     LQCD_CUDA(cudaEventCreate(&e1));
@@ -305,9 +301,12 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
     const double sb = spinor_bytes<S>();
     const int nact = a.nactive >= 0 ? std::min(a.nactive, a.nrhs) : a.nrhs;  // RHS that pass the gate
     double per_rhs = sb + (mode == RESID ? 0.0 : sb) + (mode == HOP_CLOV ? 0.0 : sb) + (mode == RESID ? sb : 0.0);
-    double shared = 8.0 * link_bytes<L>() + (mode == SELF_PLAIN ? 0.0 : clover_bytes<C>());
+    // the twisted inverse reads two Hermitian block pairs (B and C)
+    const bool twinv = a.tau != 0.0 && (mode == HOP_CLOV || mode == CLOV_SUM);
+    double shared = 8.0 * link_bytes<L>() + (mode == SELF_PLAIN ? 0.0 : (twinv ? 2.0 : 1.0) * clover_bytes<C>());
     const int pi = S::W == 2 ? 0 : (S::W == 4 ? 1 : 2);
-    if (mode == HOP_CLOV || mode == SELF_CLOV) {
+    // twisted mass runs on the generic kernel (hop_kernel) in every storage format
+    if ((mode == HOP_CLOV || mode == SELF_CLOV) && a.tau == 0.0) {
         FastHop<S> f = make_fast(a);
         const HopShape sh = hopf_tuned<S>(f, mode, st);
         f.gpb = sh.gpb;

@@ -1,6 +1,7 @@
 // Gauge-field repacking, clover-field construction and inversion, spinor
 // repacking between the host layout and the even-odd SoA layout, point
 // sources and the pion contraction.
+#include "gauge_dev.cuh"
 #include "lqcd_impl.h"
 
 namespace lqcd {
@@ -37,6 +38,21 @@ template <>
 CloverField<F16> clover_field<F16>(const CloverSet &c, bool inv, long stride)
 {
     return {(inv ? c.ainv16 : c.a16).as<const uint4>(), stride};
+}
+template <>
+CloverField<F64> clover_field_c<F64>(const CloverSet &c, long stride)
+{
+    return {c.cinv64.as<const double2>(), stride};
+}
+template <>
+CloverField<F32> clover_field_c<F32>(const CloverSet &c, long stride)
+{
+    return {c.cinv32.as<const float4>(), stride};
+}
+template <>
+CloverField<F16> clover_field_c<F16>(const CloverSet &c, long stride)
+{
+    return {c.cinv16.as<const uint4>(), stride};
 }
 
 __device__ __forceinline__ void lex_coords(const Geom &g, long s, int x[4])
@@ -97,72 +113,6 @@ void gauge_repack(lqcd_lattice_s *lat, GaugeSet &g, const double *U_dev, cudaStr
 // ---------------------------------------------------------------------------
 // clover field (Csw! of Sec. 3.3)
 // ---------------------------------------------------------------------------
-using cd = cx<double>;
-using m3 = su3<double>;
-
-__device__ __forceinline__ m3 mm(const m3 &a, const m3 &b)
-{
-    m3 r;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) r.m[i][j] = a.m[i][0] * b.m[0][j] + a.m[i][1] * b.m[1][j] + a.m[i][2] * b.m[2][j];
-    return r;
-}
-
-__device__ __forceinline__ m3 md(const m3 &a)  // a^dag
-{
-    m3 r;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) r.m[i][j] = conj(a.m[j][i]);
-    return r;
-}
-
-__device__ __forceinline__ m3 link_xy(const Geom &g, const LinkField<F64> &U, const int y[4], int mu)
-{
-    int p = (y[0] + y[1] + y[2] + y[3]) & 1;
-    return load_link<F64, double>(U, p, mu, cb_index(g, y));
-}
-
-__device__ __forceinline__ void shift(const Geom &g, const int x[4], int mu, int d, int y[4])
-{
-    for (int k = 0; k < 4; ++k) y[k] = x[k];
-    y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
-}
-
-// F_{mu nu}(x) = (Q - Q^dag)/8 made traceless, Q = sum of the four leaves
-// around x, each leaf walked mu-direction first.
-__device__ m3 field_strength(const Geom &g, const LinkField<F64> &U, const int x[4], int mu, int nu)
-{
-    int xpm[4], xpn[4], xmm[4], xmn[4], a[4], b[4], c[4];
-    shift(g, x, mu, +1, xpm);
-    shift(g, x, nu, +1, xpn);
-    shift(g, x, mu, -1, xmm);
-    shift(g, x, nu, -1, xmn);
-    shift(g, xmm, nu, +1, a);  // x - mu + nu
-    shift(g, xmm, nu, -1, b);  // x - mu - nu
-    shift(g, xpm, nu, -1, c);  // x + mu - nu
-    m3 Umx = link_xy(g, U, x, mu), Unx = link_xy(g, U, x, nu);
-    m3 q = mm(mm(Umx, link_xy(g, U, xpm, nu)), mm(md(link_xy(g, U, xpn, mu)), md(Unx)));
-    m3 t = mm(mm(Unx, md(link_xy(g, U, a, mu))), mm(md(link_xy(g, U, xmm, nu)), link_xy(g, U, xmm, mu)));
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) q.m[i][j] = q.m[i][j] + t.m[i][j];
-    t = mm(mm(md(link_xy(g, U, xmm, mu)), md(link_xy(g, U, b, nu))), mm(link_xy(g, U, b, mu), link_xy(g, U, xmn, nu)));
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) q.m[i][j] = q.m[i][j] + t.m[i][j];
-    t = mm(mm(md(link_xy(g, U, xmn, nu)), link_xy(g, U, xmn, mu)), mm(link_xy(g, U, c, nu), md(Umx)));
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) q.m[i][j] = q.m[i][j] + t.m[i][j];
-    m3 f;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) f.m[i][j] = 0.125 * (q.m[i][j] - conj(q.m[j][i]));
-    cd tr = (1.0 / 3.0) * (f.m[0][0] + f.m[1][1] + f.m[2][2]);
-    for (int i = 0; i < 3; ++i) f.m[i][i] = f.m[i][i] - tr;
-    return f;
-}
-
 // Gauss-Jordan inverse of a 6x6 complex matrix with partial pivoting.
 __device__ void invert6(cd a[6][6], cd inv[6][6])
 {
@@ -220,16 +170,21 @@ __device__ void store_block(double2 *base, long stride, long cb, int off, const 
 // A_+- = 1 - i kc sum_k s_k (x) (B_k +- E_k), B = (F_yz, F_zx, F_xy), E_k = F_kt:
 // in 2x2 spin blocks of 3x3 colour matrices with M_k = B_k +- E_k,
 //   A = [[1 - i kc M_z, -i kc (M_x - i M_y)], [-i kc (M_x + i M_y), 1 + i kc M_z]].
-__global__ void __launch_bounds__(64) clover_build_kernel(Geom g, LinkField<F64> U, double kc, double2 *a64,
-                                                          double2 *ainv64)
+// open: open time boundary (absent links across it); cfterm: 2 kappa (cF - 1),
+// added to the site term on the first and last time slice when open
+__global__ void __launch_bounds__(64) clover_build_kernel(Geom g, LinkField<F64> U, double kc, double tau, bool open,
+                                                          double cfterm, double2 *a64, double2 *ainv64,
+                                                          double2 *cinv64)
 {
     const int p = blockIdx.y;
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= g.vh) return;
     int x[4];
     cb_coords(g, p, cb, x);
-    m3 Fxy = field_strength(g, U, x, 0, 1), Fxz = field_strength(g, U, x, 0, 2), Fxt = field_strength(g, U, x, 0, 3);
-    m3 Fyz = field_strength(g, U, x, 1, 2), Fyt = field_strength(g, U, x, 1, 3), Fzt = field_strength(g, U, x, 2, 3);
+    m3 Fxy = field_strength(g, U, x, 0, 1, open), Fxz = field_strength(g, U, x, 0, 2, open);
+    m3 Fxt = field_strength(g, U, x, 0, 3, open), Fyz = field_strength(g, U, x, 1, 2, open);
+    m3 Fyt = field_strength(g, U, x, 1, 3, open), Fzt = field_strength(g, U, x, 2, 3, open);
+    const double diag = (open && (x[3] == 0 || x[3] == g.L[3] - 1)) ? 1.0 + cfterm : 1.0;
     for (int blk = 0; blk < 2; ++blk) {
         const double sg = blk == 0 ? 1.0 : -1.0;
         cd A[6][6], Ai[6][6];
@@ -238,15 +193,36 @@ __global__ void __launch_bounds__(64) clover_build_kernel(Geom g, LinkField<F64>
                 cd Mx = Fyz.m[i][j] + sg * Fxt.m[i][j];
                 cd My = (-1.0) * Fxz.m[i][j] + sg * Fyt.m[i][j];
                 cd Mz = Fxy.m[i][j] + sg * Fzt.m[i][j];
-                cd id = cd{i == j ? 1.0 : 0.0, 0.0};
+                cd id = cd{i == j ? diag : 0.0, 0.0};
                 A[i][j] = id - kc * mul_i(Mz);
                 A[3 + i][3 + j] = id + kc * mul_i(Mz);
                 A[i][3 + j] = (-kc) * mul_i(Mx - mul_i(My));
                 A[3 + i][j] = (-kc) * mul_i(Mx + mul_i(My));
             }
         store_block(a64 + (long)p * 36 * g.stride, g.stride, cb, 18 * blk, A);
-        invert6(A, Ai);
-        store_block(ainv64 + (long)p * 36 * g.stride, g.stride, cb, 18 * blk, Ai);
+        if (tau == 0.0) {
+            invert6(A, Ai);
+            store_block(ainv64 + (long)p * 36 * g.stride, g.stride, cb, 18 * blk, Ai);
+        } else {
+            // twisted block A + i s tau (s = +1 upper, -1 lower): its inverse is
+            // B - i s tau C with C = (A^2 + tau^2)^-1 and B = A C (A Hermitian)
+            cd M[6][6], Ci[6][6], B[6][6];
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    cd acc = cd{i == j ? tau * tau : 0.0, 0.0};
+                    for (int k = 0; k < 6; ++k) acc = acc + A[i][k] * A[k][j];
+                    M[i][j] = acc;
+                }
+            invert6(M, Ci);
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    cd acc = cd{0.0, 0.0};
+                    for (int k = 0; k < 6; ++k) acc = acc + A[i][k] * Ci[k][j];
+                    B[i][j] = acc;
+                }
+            store_block(ainv64 + (long)p * 36 * g.stride, g.stride, cb, 18 * blk, B);
+            store_block(cinv64 + (long)p * 36 * g.stride, g.stride, cb, 18 * blk, Ci);
+        }
     }
 }
 
@@ -273,9 +249,9 @@ __global__ void clover_convert_kernel(long vh, long stride, const double2 *src, 
     }
 }
 
-size_t clover_bytes(const lqcd_lattice_s *lat)
+size_t clover_bytes(const lqcd_lattice_s *lat, bool twisted)
 {
-    return 2 * 2 * (size_t)lat->stride * (36 * sizeof(double2) + 18 * sizeof(float4) + 9 * sizeof(uint4));
+    return (twisted ? 3 : 2) * 2 * (size_t)lat->stride * (36 * sizeof(double2) + 18 * sizeof(float4) + 9 * sizeof(uint4));
 }
 
 size_t gauge_bytes(const lqcd_lattice_s *lat)
@@ -283,13 +259,18 @@ size_t gauge_bytes(const lqcd_lattice_s *lat)
     return 2 * 4 * (size_t)lat->stride * (9 * sizeof(double2) + 3 * sizeof(float4) + sizeof(uint4) + sizeof(uint2));
 }
 
-std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st,
-                                        bool async)
+std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp,
+                                        cudaStream_t st, bool async)
 {
-    const double kc = kappa * csw;
+    const double kc = dp.kappa * dp.csw;
+    const bool open = dp.bc == LQCD_BC_OPEN;
     auto c = std::make_unique<CloverSet>();
+    c->tau = 2.0 * dp.kappa * dp.mu;
+    const bool tw = c->tau != 0.0;
     if (async)
-        for (DevBuf *b : {&c->a64, &c->ainv64, &c->a32, &c->ainv32, &c->a16, &c->ainv16}) b->set_async(st);
+        for (DevBuf *b : {&c->a64, &c->ainv64, &c->cinv64, &c->a32, &c->ainv32, &c->cinv32, &c->a16, &c->ainv16,
+                          &c->cinv16})
+            b->set_async(st);
     const long S = lat->stride;
     c->a64.ensure(sizeof(double2) * 2 * 36 * S);
     c->ainv64.ensure(sizeof(double2) * 2 * 36 * S);
@@ -297,28 +278,48 @@ std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, double
     c->ainv32.ensure(sizeof(float4) * 2 * 18 * S);
     c->a16.ensure(sizeof(uint4) * 2 * 9 * S);
     c->ainv16.ensure(sizeof(uint4) * 2 * 9 * S);
+    if (tw) {
+        c->cinv64.ensure(sizeof(double2) * 2 * 36 * S);
+        c->cinv32.ensure(sizeof(float4) * 2 * 18 * S);
+        c->cinv16.ensure(sizeof(uint4) * 2 * 9 * S);
+    }
     dim3 grid(unsigned((lat->vh + 63) / 64), 2);
-    ProfScope prof("clover_build", double(lat->V) * (4 * 144.0 + 2 * 576.0), st);
-    clover_build_kernel<<<grid, 64, 0, st>>>(lat->geom, link_field<F64>(g, S), kc, c->a64.as<double2>(),
-                                             c->ainv64.as<double2>());
+    ProfScope prof("clover_build", double(lat->V) * (4 * 144.0 + (tw ? 3 : 2) * 576.0), st);
+    clover_build_kernel<<<grid, 64, 0, st>>>(lat->geom, link_field<F64>(g, S), kc, c->tau, open,
+                                             open ? 2.0 * dp.kappa * (dp.cF - 1.0) : 0.0, c->a64.as<double2>(),
+                                             c->ainv64.as<double2>(), tw ? c->cinv64.as<double2>() : nullptr);
     LQCD_CHECK_LAUNCH();
     dim3 g2(unsigned((lat->vh + kBlock - 1) / kBlock), 2);
     clover_convert_kernel<<<g2, kBlock, 0, st>>>(lat->vh, S, c->a64.as<const double2>(), c->a32.as<float4>(),
                                                  c->a16.as<uint4>());
     clover_convert_kernel<<<g2, kBlock, 0, st>>>(lat->vh, S, c->ainv64.as<const double2>(), c->ainv32.as<float4>(),
                                                  c->ainv16.as<uint4>());
+    if (tw)
+        clover_convert_kernel<<<g2, kBlock, 0, st>>>(lat->vh, S, c->cinv64.as<const double2>(), c->cinv32.as<float4>(),
+                                                     c->cinv16.as<uint4>());
     LQCD_CHECK_LAUNCH();
     return c;
 }
 
-CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st)
+void hop_theta(const lqcd_dirac_params &dp, double th_re[4], double th_im[4])
 {
-    const double kc = kappa * csw;
-    auto it = g.clover.find(kc);
+    for (int mu = 0; mu < 4; ++mu) {
+        th_re[mu] = dp.theta_re[mu];
+        th_im[mu] = dp.theta_im[mu];
+    }
+    if (dp.bc == LQCD_BC_OPEN) th_re[3] = th_im[3] = 0.0;  // the hops across the time boundary vanish
+}
+
+CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, cudaStream_t st)
+{
+    const bool open = dp.bc == LQCD_BC_OPEN;
+    const auto key = std::make_tuple(dp.kappa * dp.csw, dp.kappa * dp.mu, int(open),
+                                     open ? dp.kappa * (dp.cF - 1.0) : 0.0);
+    auto it = g.clover.find(key);
     if (it != g.clover.end()) return *it->second;
-    auto c = clover_build(lat, g, kappa, csw, st, false);
+    auto c = clover_build(lat, g, dp, st, false);
     CloverSet &ref = *c;
-    g.clover.emplace(kc, std::move(c));
+    g.clover.emplace(key, std::move(c));
     return ref;
 }
 
@@ -393,31 +394,9 @@ void point_sources(lqcd_lattice_s *lat, const int src[4], SpinorField<F64> even,
 // ---------------------------------------------------------------------------
 // pion contraction: corr[(t - src_t) mod T] = sum over the time slice t of
 // |S_j|^2 for the 12 columns, FP64.  Blocks (c, t) sum one chunk of slice t
-// and the last block of the slice adds the chunks in a fixed order.
+// and the last block of the slice adds the chunks in a fixed order
+// (slice_finish, gauge_dev.cuh).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void slice_finish(double v, int t, int c, int nchunk, int T, int src_t, double *partial,
-                                             unsigned *counter, double *corr)
-{
-    __shared__ double sh[32];
-    __shared__ int last;
-    double s = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        partial[(long)t * nchunk + c] = s;
-        __threadfence();
-        last = atomicAdd(&counter[t], 1u) == unsigned(nchunk - 1);
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        double a = 0.0;
-        for (int k = threadIdx.x; k < nchunk; k += blockDim.x) a += __ldcg(partial + (long)t * nchunk + k);
-        a = block_sum(a, sh);
-        if (threadIdx.x == 0) {
-            counter[t] = 0;
-            corr[((t - src_t) % T + T) % T] = a;
-        }
-    }
-}
 
 // SoA columns: slice t of parity p is cb range [t V3h, (t+1) V3h)
 __global__ void __launch_bounds__(128) contract_soa_kernel(long v3h, int T, int src_t, SpinorField<F64> ev,
@@ -467,6 +446,68 @@ void pion_contract_soa(lqcd_lattice_s *lat, SpinorField<F64> even, SpinorField<F
     const int nchunk = int((v3h + kBlock - 1) / kBlock);
     ProfScope prof("pion_contract", double(lat->V) * 12 * 192.0, st);
     contract_soa_kernel<<<dim3(nchunk, T), kBlock, 0, st>>>(v3h, T, src_t, even, odd, partial, counter, corr_dev);
+    LQCD_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// boundary-to-bulk correlators (open boundary)
+// ---------------------------------------------------------------------------
+// column j (j = 3 s + c, s < 2) at every site of slice 0: (P+ e_j)_al = (delta_{al,s} + (g_t)_{al,s}) / 2,
+// with g_t = [[0, -1], [-1, 0]] in 2x2 spin blocks: P+ e_s = (e_s - e_{s+2}) / 2
+__global__ void wall_source_kernel(long V, long v3, double *aos)
+{
+    const long i = long(blockIdx.x) * blockDim.x + threadIdx.x;  // (j, site) over 6 V
+    if (i >= 6 * V) return;
+    const int j = int(i / V);
+    const long x = i - long(j) * V;
+    double *o = aos + i * 24;
+    for (int k = 0; k < 24; ++k) o[k] = 0.0;
+    if (x < v3) {
+        const int s = j / 3, c = j % 3;
+        o[2 * (3 * s + c)] = 0.5;
+        o[2 * (3 * (s + 2) + c)] = -0.5;
+    }
+}
+
+void wall_sources_p_plus(lqcd_lattice_s *lat, double *aos, cudaStream_t st)
+{
+    const long n = 6 * lat->V;
+    ProfScope prof("wall_source", double(n) * 192.0, st);
+    wall_source_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(lat->V, lat->V / lat->dims[3], aos);
+    LQCD_CHECK_LAUNCH();
+}
+
+// per site: sum_j |h_j|^2 and -sum_j Re <h_j, g_t h_j>; with g_t mixing spin s and s + 2 by -1:
+// <h, g_t h> = -sum_{s<2, c} 2 Re(conj(h_s) h_{s+2})
+__global__ void __launch_bounds__(128) boundary_contract_kernel(long V, long v3, int T, const double *H,
+                                                                double *partial, unsigned *counter, double *fP,
+                                                                double *fA)
+{
+    const int t = blockIdx.y, c = blockIdx.x, nchunk = gridDim.x;
+    const long x = long(c) * blockDim.x + threadIdx.x;
+    double p = 0.0, a = 0.0;
+    if (x < v3) {
+        for (int j = 0; j < 6; ++j) {
+            const double *h = H + ((long)j * V + (long)t * v3 + x) * 24;
+            for (int k = 0; k < 24; ++k) p += h[k] * h[k];
+            for (int q = 0; q < 6; ++q) {  // q = 3 s + colour, s < 2: pair with 3 (s + 2) + colour
+                const double ur = h[2 * q], ui = h[2 * q + 1], dr = h[2 * (q + 6)], di = h[2 * (q + 6) + 1];
+                a += 2.0 * (ur * dr + ui * di);  // -Re <h, g_t h>
+            }
+        }
+    }
+    slice_finish(p, t, c, nchunk, T, 0, partial, counter, fP);
+    slice_finish(a, t, c, nchunk, T, 0, partial + (long)T * nchunk, counter + T, fA);
+}
+
+void boundary_contract(lqcd_lattice_s *lat, const double *H_dev, double *fP, double *fA, double *partial,
+                       unsigned *counter, cudaStream_t st)
+{
+    const int T = lat->dims[3];
+    const long v3 = lat->V / T;
+    const int nchunk = int((v3 + kBlock - 1) / kBlock);
+    ProfScope prof("boundary_contract", double(lat->V) * 6 * 192.0, st);
+    boundary_contract_kernel<<<dim3(nchunk, T), kBlock, 0, st>>>(lat->V, v3, T, H_dev, partial, counter, fP, fA);
     LQCD_CHECK_LAUNCH();
 }
 

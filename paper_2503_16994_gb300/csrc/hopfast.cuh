@@ -891,13 +891,61 @@ __device__ __forceinline__ void accumulate_s(cp acc[12], const cp g[2][3], float
     }
 }
 
+// colour c of accumulate_s: acc += sc (1 + S g_mu) psi from (g0, g1) = g[0][c], g[1][c]
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_row(cp acc[12], int c, const cp &g0, const cp &g1, float2 sc, float2 nsc)
+{
+    const float2 ps = S > 0 ? sc : nsc, ms = S > 0 ? nsc : sc;  // S sc, -S sc
+    acc[c] = cp{p_fma(g0.r, sc, acc[c].r), p_fma(g0.i, sc, acc[c].i)};
+    acc[3 + c] = cp{p_fma(g1.r, sc, acc[3 + c].r), p_fma(g1.i, sc, acc[3 + c].i)};
+    cp &l0 = acc[6 + c], &l1 = acc[9 + c];
+    if (MU == 0) {  // lower += S (i g1, i g0)
+        l0 = cp{p_fma(g1.i, ms, l0.r), p_fma(g1.r, ps, l0.i)};
+        l1 = cp{p_fma(g0.i, ms, l1.r), p_fma(g0.r, ps, l1.i)};
+    } else if (MU == 1) {  // lower += S (g1, -g0)
+        l0 = cp{p_fma(g1.r, ps, l0.r), p_fma(g1.i, ps, l0.i)};
+        l1 = cp{p_fma(g0.r, ms, l1.r), p_fma(g0.i, ms, l1.i)};
+    } else if (MU == 2) {  // lower += S (i g0, -i g1)
+        l0 = cp{p_fma(g0.i, ms, l0.r), p_fma(g0.r, ps, l0.i)};
+        l1 = cp{p_fma(g1.i, ps, l1.r), p_fma(g1.r, ms, l1.i)};
+    } else {  // lower -= S (g0, g1)
+        l0 = cp{p_fma(g0.r, ms, l0.r), p_fma(g0.i, ms, l0.i)};
+        l1 = cp{p_fma(g1.r, ms, l1.r), p_fma(g1.i, ms, l1.i)};
+    }
+}
+
+// row a of g = U h or U^dag h for both lanes: the operations of link_mul_u for one colour row
+template <bool DAGU>
+__device__ __forceinline__ void link_row_u(const float u[18], int a, const cp h[2][3], cp &g0, cp &g1)
+{
+    cp acc0{bc(0.f), bc(0.f)}, acc1{bc(0.f), bc(0.f)};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const int k = DAGU ? 2 * (3 * b + a) : 2 * (3 * a + b);
+        const float2 ur = bc(u[k]), ui = bc(u[k + 1]), nui = bc(-u[k + 1]);
+        const float2 x1 = DAGU ? ui : nui, x2 = DAGU ? nui : ui;
+        acc0.r = p_fma(ur, h[0][b].r, acc0.r);
+        acc0.r = p_fma(x1, h[0][b].i, acc0.r);
+        acc0.i = p_fma(ur, h[0][b].i, acc0.i);
+        acc0.i = p_fma(x2, h[0][b].r, acc0.i);
+        acc1.r = p_fma(ur, h[1][b].r, acc1.r);
+        acc1.r = p_fma(x1, h[1][b].i, acc1.r);
+        acc1.i = p_fma(ur, h[1][b].i, acc1.i);
+        acc1.i = p_fma(x2, h[1][b].r, acc1.i);
+    }
+    g0 = acc0;
+    g1 = acc1;
+}
+
 // one direction of a pair of right-hand sides from their FP16 words (wa, wb,
-// scales sa, sb) and the decoded link u
+// scales sa, sb) and the decoded link u; each colour row of the link product
+// is phased and accumulated as soon as it is formed (the element-wise
+// operations of link_mul_u, the phase and accumulate_s, so the same bits)
 template <class S, int MU, int DIR, int SP>
 __device__ __forceinline__ void dir_words(const FastHop<S> &a, const float u[18], const __half2 wa[12],
                                           const __half2 wb[12], float sa, float sb, bool wrap, cp acc[12])
 {
-    cp h[2][3], g[2][3];
+    cp h[2][3];
     __half2 ha[2][3], hb[2][3];
     project_h<MU, SP>(wa, ha);
     project_h<MU, SP>(wb, hb);
@@ -907,19 +955,20 @@ __device__ __forceinline__ void dir_words(const FastHop<S> &a, const float u[18]
         for (int c = 0; c < 3; ++c)
             h[s][c] = cp{make_float2(__low2float(ha[s][c]), __low2float(hb[s][c])),
                          make_float2(__high2float(ha[s][c]), __high2float(hb[s][c]))};
-    link_mul_u<(DIR < 0)>(u, h, g);
-    if (wrap && ((a.theta_mask >> MU) & 1)) {
-        const float2 pr = bc(float(a.th_re[MU])), pi = bc(DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]));
-        const float2 npi = bc(DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]));
+    const bool phase = wrap && ((a.theta_mask >> MU) & 1);
+    const float2 sc = make_float2(sa, sb), nsc = make_float2(-sa, -sb);
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const cp x = g[s][c];
-                g[s][c] = cp{p_fma(npi, x.i, p_mul(pr, x.r)), p_fma(pi, x.r, p_mul(pr, x.i))};
-            }
+    for (int c = 0; c < 3; ++c) {
+        cp g0, g1;
+        link_row_u<(DIR < 0)>(u, c, h, g0, g1);
+        if (phase) {
+            const float2 pr = bc(float(a.th_re[MU])), pi = bc(DIR > 0 ? float(a.th_im[MU]) : float(-a.th_im[MU]));
+            const float2 npi = bc(DIR > 0 ? float(-a.th_im[MU]) : float(a.th_im[MU]));
+            g0 = cp{p_fma(npi, g0.i, p_mul(pr, g0.r)), p_fma(pi, g0.r, p_mul(pr, g0.i))};
+            g1 = cp{p_fma(npi, g1.i, p_mul(pr, g1.r)), p_fma(pi, g1.r, p_mul(pr, g1.i))};
+        }
+        accumulate_row<MU, SP>(acc, c, g0, g1, sc, nsc);
     }
-    accumulate_s<MU, SP>(acc, g, make_float2(sa, sb), make_float2(-sa, -sb));
 }
 
 template <class S, int MU, int DIR, int SG>

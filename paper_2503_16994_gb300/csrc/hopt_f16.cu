@@ -7,10 +7,10 @@
 
 namespace lqcd {
 
-template <int MODE, bool DAG, bool NORM, int MINB, bool PF>
+template <int MODE, bool DAG, bool NORM, int MINB, int PD>
 static void hopt_launch(const FastHop<F16> &f, int npw, cudaStream_t st)
 {
-    constexpr int smem = tile_smem_bytes();
+    constexpr int smem_max = tile_smem_bytes(kTileSites * kTileMaxPairs, PD);
     // more than the 48 KB a block gets without opting in: the opt-in is a
     // per-device attribute, set the first time the kernel runs on each device
     // (the autotuner's eager launches, before any stream capture)
@@ -21,8 +21,8 @@ static void hopt_launch(const FastHop<F16> &f, int npw, cudaStream_t st)
     {
         std::lock_guard<std::mutex> lk(mu);
         if (opted.insert(dev).second) {
-            const cudaError_t e = cudaFuncSetAttribute(hopt_kernel<MODE, DAG, NORM, MINB, PF>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            const cudaError_t e = cudaFuncSetAttribute(hopt_kernel<MODE, DAG, NORM, MINB, PD>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
             if (e != cudaSuccess) {
                 opted.erase(dev);
                 LQCD_CUDA(e);
@@ -32,24 +32,20 @@ static void hopt_launch(const FastHop<F16> &f, int npw, cudaStream_t st)
     const int npairs = (f.nrhs + 1) / 2;
     const int nbt = (npairs + npw - 1) / npw;
     const unsigned grid = unsigned(4L * f.ntiles * nbt);
-    hopt_kernel<MODE, DAG, NORM, MINB, PF><<<grid, unsigned(kTileSites * npw), smem, st>>>(f);
+    hopt_kernel<MODE, DAG, NORM, MINB, PD>
+        <<<grid, unsigned(kTileSites * npw), tile_smem_bytes(kTileSites * npw, PD), st>>>(f);
 }
 
 template <int MODE, bool DAG, bool NORM>
 static void hopt_go(const FastHop<F16> &f, bool pf, cudaStream_t st)
 {
     const int npw = std::max(1, std::min(f.gpb, kTileMaxPairs));
-    if (pf) {
-        if (f.minb >= 3) hopt_launch<MODE, DAG, NORM, 3, true>(f, npw, st);
-        else hopt_launch<MODE, DAG, NORM, 2, true>(f, npw, st);
-    } else {
-        if (f.minb >= 3) hopt_launch<MODE, DAG, NORM, 3, false>(f, npw, st);
-        else hopt_launch<MODE, DAG, NORM, 2, false>(f, npw, st);
-    }
+    if (pf) hopt_launch<MODE, DAG, NORM, 2, 2>(f, npw, st);
+    else hopt_launch<MODE, DAG, NORM, 2, 1>(f, npw, st);
 }
 
-// gpb: pairs of right-hand sides (warps) per block, minb: resident blocks
-// per SM the registers are capped for (2 or 3), pf: prefetch one direction
+// gpb: pairs of right-hand sides (warps) per block; pf: spinor words staged
+// two directions ahead instead of one (registers capped for 2 blocks per SM)
 void hopt_dispatch(const FastHop<F16> &f, bool pf, int mode, bool dag, bool norm, cudaStream_t st)
 {
     if (mode == HOP_CLOV) {

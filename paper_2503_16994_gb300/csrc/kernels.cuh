@@ -38,7 +38,8 @@ enum RedOp : int {
     RED_ALPHA = 2,   // alpha = gamma / sum
     RED_BETA = 3,    // beta = sum / gamma (0 on the first pass); gamma = sum
     RED_RUPDATE = 4, // rr = sum; iter++; request an FP64 residual when due
-    RED_RHAT = 5     // sum = |FP64 residual|^2: finish, or resume the inner iteration
+    RED_RHAT = 5,    // sum = |FP64 residual|^2: finish, or resume the inner iteration
+    RED_RHAT_COARSE = 6  // sum = |residual|^2 recomputed with an FP32 operator: resume (never finishes)
 };
 
 struct Reduce {
@@ -77,6 +78,11 @@ __device__ __forceinline__ void apply_op(const Reduce &r, int j, double sum)
             s.status = ST_MAXITER;
         else
             s.status = s.resume;
+        break;
+    case RED_RHAT_COARSE:
+        s.rr = sum / (s.scale * s.scale);
+        s.rr_ref = s.rr;
+        s.status = (sum == sum) ? s.resume : ST_UPDATE;  // a NaN goes to the FP64 update
         break;
     }
 }
@@ -187,6 +193,8 @@ struct HopArgs {
     SpinorField<S> in, self, out, b;
     LinkField<L> U;
     CloverField<C> clov;   // clover blocks used by the epilogue (output parity taken from `parity`)
+    CloverField<C> clov2;  // twisted mass: the C blocks of the inverse (clov then holds B), else unused
+    double tau;            // twisted mass 2 kappa mu of the site term (0: none); the dagger uses -tau
     double coef;
     double th_re[4], th_im[4];
     const RhsState *gate_st;  // nullptr: every RHS runs
@@ -228,6 +236,29 @@ template <typename R> __device__ __forceinline__ spinor<R> axpy_sp(R c, const sp
     return r;
 }
 
+// out += i t g5 v: in the chiral basis g5 = +1 on spins 0, 1 and -1 on spins
+// 2, 3, so the twisted-mass site term i tau g5 is a diagonal phase
+template <typename R> __device__ __forceinline__ void add_twist(spinor<R> &out, R t, const spinor<R> &v)
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const R ts = s < 2 ? t : -t;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out.s[s][k] = out.s[s][k] + ts * mul_i(v.s[s][k]);
+    }
+}
+
+// (A + i t g5)^-1 v = (B - i t g5 C) v for the Hermitian blocks B = A C and
+// C = (A^2 + t^2)^-1 of each chirality (A Hermitian)
+template <typename R>
+__device__ __forceinline__ spinor<R> twisted_inverse(const clover_block<R> B[2], const clover_block<R> C[2], R t,
+                                                     const spinor<R> &v)
+{
+    spinor<R> r = clover_apply(B, v);
+    add_twist(r, -t, clover_apply(C, v));
+    return r;
+}
+
 template <typename R> __device__ __forceinline__ double norm2_sp(const spinor<R> &x)
 {
     R acc = R(0);
@@ -257,11 +288,19 @@ __global__ void __launch_bounds__(128) hop_kernel(const HopArgs<S, L, C> a)
         hop_dir<S, L, C, R, 2, SG>(a, j, i, x, acc);
         hop_dir<S, L, C, R, 3, SG>(a, j, i, x, acc);
         const R coef = R(a.coef);
+        // twisted mass: the site term is A + i tau g5, its adjoint takes -tau
+        const R tau = R(DAG ? -a.tau : a.tau);
         spinor<R> res;
         if constexpr (MODE == HOP_CLOV) {
             clover_block<R> blk[2];
             load_clover<C, R>(a.clov, a.parity, i, blk);
-            res = clover_apply(blk, acc);
+            if (tau != R(0)) {
+                clover_block<R> blk2[2];
+                load_clover<C, R>(a.clov2, a.parity, i, blk2);
+                res = twisted_inverse(blk, blk2, tau, acc);
+            } else {
+                res = clover_apply(blk, acc);
+            }
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -271,11 +310,21 @@ __global__ void __launch_bounds__(128) hop_kernel(const HopArgs<S, L, C> a)
         } else if constexpr (MODE == CLOV_SUM) {
             clover_block<R> blk[2];
             load_clover<C, R>(a.clov, a.parity, i, blk);
-            res = clover_apply(blk, axpy_sp(coef, acc, load_spinor<S, R>(a.self, j, i)));
+            const spinor<R> v = axpy_sp(coef, acc, load_spinor<S, R>(a.self, j, i));
+            if (tau != R(0)) {
+                clover_block<R> blk2[2];
+                load_clover<C, R>(a.clov2, a.parity, i, blk2);
+                res = twisted_inverse(blk, blk2, tau, v);
+            } else {
+                res = clover_apply(blk, v);
+            }
         } else {  // SELF_CLOV, RESID
             clover_block<R> blk[2];
             load_clover<C, R>(a.clov, a.parity, i, blk);
-            res = axpy_sp(coef, acc, clover_apply(blk, load_spinor<S, R>(a.self, j, i)));
+            const spinor<R> sv = load_spinor<S, R>(a.self, j, i);
+            spinor<R> site = clover_apply(blk, sv);
+            if (tau != R(0)) add_twist(site, tau, sv);
+            res = axpy_sp(coef, acc, site);
         }
         if constexpr (MODE == RESID) {
             res = axpy_sp(R(-1), res, load_spinor<S, R>(a.b, j, i));
@@ -350,9 +399,10 @@ __global__ void __launch_bounds__(128) cg_x_update(VecArgs v, const RhsState *st
     store_spinor<E, double>(e, j, i, z);
 }
 
-// rhat = bhat - w (FP64); r = rhat / scale (low precision); |rhat|^2 -> RED_RHAT
-template <class W>
-__global__ void __launch_bounds__(128) cg_r_replace(VecArgs v, SpinorField<F64> bhat, SpinorField<F64> w,
+// rhat = bhat - w (FP64 arithmetic; w in FP64, or FP32 for a coarse
+// update); r = rhat / scale (low precision); |rhat|^2 -> RED_RHAT(_COARSE)
+template <class W, class WI>
+__global__ void __launch_bounds__(128) cg_r_replace(VecArgs v, SpinorField<F64> bhat, SpinorField<WI> w,
                                                     SpinorField<W> r)
 {
     const int j = blockIdx.x % v.nrhs, tile = blockIdx.x / v.nrhs;
@@ -360,7 +410,7 @@ __global__ void __launch_bounds__(128) cg_r_replace(VecArgs v, SpinorField<F64> 
     const int i = tile * blockDim.x + threadIdx.x;
     double n2 = 0.0;
     if (i < v.vh) {
-        spinor<double> rh = axpy_sp(-1.0, load_spinor<F64, double>(w, j, i), load_spinor<F64, double>(bhat, j, i));
+        spinor<double> rh = axpy_sp(-1.0, load_spinor<WI, double>(w, j, i), load_spinor<F64, double>(bhat, j, i));
         n2 = norm2_sp(rh);
         const double inv = 1.0 / v.red.st[j].scale;
         using R = typename std::conditional<std::is_same<W, F64>::value, double, float>::type;
@@ -384,10 +434,12 @@ __global__ void __launch_bounds__(128) convert_kernel(int vh, int nrhs, SpinorFi
     store_spinor<SO, double>(out, j, i, load_spinor<SI, double>(in, j, i));
 }
 
-// out = C in (clover blocks of parity `parity`)
+// out = C in (clover blocks of parity `parity`); with tau != 0 the twisted
+// inverse (B - i tau g5 C2) in, cl holding B and cl2 C
 template <class S, class C>
 __global__ void __launch_bounds__(128) clover_apply_kernel(int vh, int nrhs, int parity, CloverField<C> cl,
-                                                           SpinorField<S> in, SpinorField<S> out)
+                                                           SpinorField<S> in, SpinorField<S> out, double tau,
+                                                           CloverField<C> cl2)
 {
     const int j = blockIdx.x % nrhs, tile = blockIdx.x / nrhs;
     const int i = tile * blockDim.x + threadIdx.x;
@@ -395,7 +447,14 @@ __global__ void __launch_bounds__(128) clover_apply_kernel(int vh, int nrhs, int
     using R = typename std::conditional<std::is_same<S, F64>::value, double, float>::type;
     clover_block<R> blk[2];
     load_clover<C, R>(cl, parity, i, blk);
-    store_spinor<S, R>(out, j, i, clover_apply(blk, load_spinor<S, R>(in, j, i)));
+    const spinor<R> v = load_spinor<S, R>(in, j, i);
+    if (tau != 0.0) {
+        clover_block<R> blk2[2];
+        load_clover<C, R>(cl2, parity, i, blk2);
+        store_spinor<S, R>(out, j, i, twisted_inverse(blk, blk2, R(tau), v));
+    } else {
+        store_spinor<S, R>(out, j, i, clover_apply(blk, v));
+    }
 }
 
 }  // namespace lqcd

@@ -86,22 +86,31 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 // resident fields
 // ---------------------------------------------------------------------------
+// Clover site terms of one (gauge field, kappa csw, twisted mass): A, the
+// Hermitian chirality blocks, and the inverse of A + i tau g5 (tau = 2 kappa
+// mu).  tau = 0: ainv = A^-1.  tau != 0: per block (sign s = +1 upper, -1
+// lower) (A + i s tau)^-1 = B - i s tau C with C = (A^2 + tau^2)^-1 and
+// B = A C, both Hermitian; ainv holds B and cinv holds C.
 struct CloverSet {
-    DevBuf a64, ainv64;  // [parity][36 double2 planes]
-    DevBuf a32, ainv32;  // [parity][18 float4 planes]
-    DevBuf a16, ainv16;  // [parity][9 uint4 planes]
+    double tau = 0.0;
+    DevBuf a64, ainv64, cinv64;  // [parity][36 double2 planes]
+    DevBuf a32, ainv32, cinv32;  // [parity][18 float4 planes]
+    DevBuf a16, ainv16, cinv16;  // [parity][9 uint4 planes]
 };
 
 struct GaugeSet {
     DevBuf u64;             // [parity][mu][9 double2 planes]
     DevBuf u32;             // [parity][mu][3 float4 planes]
     DevBuf u16, u16b;       // [parity][mu] uint4 plane + uint2 plane
-    std::map<double, std::unique_ptr<CloverSet>> clover;  // keyed by kappa * csw
+    // keyed by (kappa csw, kappa mu, open, kappa (cF - 1))
+    std::map<std::tuple<double, double, int, double>, std::unique_ptr<CloverSet>> clover;
 };
 
 // Storage-format-specific field pointers for one (gauge, clover) pair.
 template <class S> LinkField<S> link_field(const GaugeSet &g, long stride);
 template <class S> CloverField<S> clover_field(const CloverSet &c, bool inverse, long stride);
+// the C blocks of a twisted inverse (null pointers when tau = 0)
+template <class S> CloverField<S> clover_field_c(const CloverSet &c, long stride);
 
 // Solver workspace for one (nrhs, precision): fields of one parity each.
 struct Workspace {
@@ -123,9 +132,9 @@ struct Workspace {
 // pageable memory.
 std::unique_ptr<Workspace> workspace_build(lqcd_lattice_s *lat, int nrhs, int prec, cudaStream_t st, bool async);
 size_t workspace_bytes(const lqcd_lattice_s *lat, int nrhs, int prec);
-std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st,
-                                        bool async);
-size_t clover_bytes(const lqcd_lattice_s *lat);
+std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp,
+                                        cudaStream_t st, bool async);
+size_t clover_bytes(const lqcd_lattice_s *lat, bool twisted = false);
 size_t gauge_bytes(const lqcd_lattice_s *lat);
 
 }  // namespace lqcd
@@ -174,7 +183,17 @@ inline int ntiles_of(long vh) { return int((vh + kBlock - 1) / kBlock); }
 
 // gauge / clover setup (field_ops.cu)
 void gauge_repack(lqcd_lattice_s *lat, GaugeSet &g, const double *U_dev_aos, cudaStream_t st);
-CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, double kappa, double csw, cudaStream_t st);
+CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, cudaStream_t st);
+// the boundary phases the hopping kernels use: theta, with theta_t = 0 for an open time boundary
+void hop_theta(const lqcd_dirac_params &dp, double th_re[4], double th_im[4]);
+
+// Wilson flow of the resident links (RK3, nsteps of eps; FP32/FP16 copies
+// rebuilt, clover cache dropped), per-slice observables into out_dev[4 T]
+// (plaquette / 3, plaquette and clover action densities, clover charge
+// density), and the links in the host layout (gauge_flow.cu)
+void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaStream_t st);
+void gauge_observables(lqcd_lattice_s *lat, GaugeSet &g, double *out_dev, cudaStream_t st);
+void gauge_download(lqcd_lattice_s *lat, GaugeSet &g, double *U_dev, cudaStream_t st);
 
 // host-layout <-> even-odd SoA FP64 (field_ops.cu)
 void spinor_to_soa(lqcd_lattice_s *lat, const double *aos, int nrhs, SpinorField<F64> even, SpinorField<F64> odd,
@@ -189,6 +208,11 @@ void pion_contract_soa(lqcd_lattice_s *lat, SpinorField<F64> even, SpinorField<F
 // corr[t] from 12 host-layout columns already on the device
 void pion_contract_aos(lqcd_lattice_s *lat, const double *prop_dev, int src_t, double *corr_dev,
                        double *partial, unsigned *counter, cudaStream_t st);
+// the six boundary wall sources delta_{y_t,0} P+ e_j (j = 3 s + c, s < 2), host layout, on the device
+void wall_sources_p_plus(lqcd_lattice_s *lat, double *aos, cudaStream_t st);
+// fP[t], fA[t] (device, T doubles each) from six host-layout columns on the device
+void boundary_contract(lqcd_lattice_s *lat, const double *H_dev, double *fP, double *fA, double *partial,
+                       unsigned *counter, cudaStream_t st);
 // corr[g][t] (complex) for ng host 4x4 spin matrices, 12 host-layout columns on the device (meson.cu)
 void meson_contract(lqcd_lattice_s *lat, const double *prop_dev, int src_t, const double *gammas, int ng,
                     double *corr_dev, cudaStream_t st);
@@ -205,17 +229,18 @@ template <class W>
 void launch_p_update(const VecArgs &v, const RhsState *s, SpinorField<W> z, SpinorField<W> p, cudaStream_t st);
 template <class E>
 void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, SpinorField<F64> x, cudaStream_t st);
-template <class W>
-void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<F64> w, SpinorField<W> r,
+template <class W, class WI>
+void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<WI> w, SpinorField<W> r,
                       cudaStream_t st);
 void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st);
 // finishes the per-tile partials a hopping kernel wrote with reduce_partial
 // (quad: the FP32 32-site partials of the tile kernel in r.partial_f)
 void launch_partial_finish(const Reduce &r, int ntiles, int nrhs, const RhsState *gate_st, int gate, cudaStream_t st,
                            bool quad = false);
+// out = C in, or with tau != 0 the twisted inverse (B - i s tau Cc) in (cl = B, cl2 = Cc)
 template <class S, class C>
 void launch_clover_apply(long vh, int nrhs, int parity, CloverField<C> cl, SpinorField<S> in, SpinorField<S> out,
-                         cudaStream_t st);
+                         cudaStream_t st, double tau = 0.0, CloverField<C> cl2 = CloverField<C>{});
 
 template <class SI, class SO>
 void launch_convert(long vh, int nrhs, SpinorField<SI> in, SpinorField<SO> out, cudaStream_t st);

@@ -92,14 +92,14 @@ void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, 
     static const char *modes[] = {"hopclov", "selfclov", "self", "clovsum", "resid"};
     // shape code nr: 1-3 scalar (nr RHS per thread), 0 paired, -2/-4/-8
     // prefetching (loads of that many directions ahead), 12/13 paired with
-    // 2/3 directions staged in shared memory, 20/21 tile kernel (links,
-    // clover and neighbours shared by the block; gpb = pairs per block, 21
-    // with one direction of loads ahead)
+    // 2/3 directions staged in shared memory, 20/21 tile kernel (links and
+    // clover shared by the block, gpb = pairs per block; spinor words staged
+    // 1 or 2 directions ahead)
     const bool tile = nr == 20 || nr == 21;
     const char *variant = tile ? "paired_tile"
                                : (nr >= 12 ? "paired_staged" : (nr == 0 ? "paired" : (nr < 0 ? "prefetch" : "scalar")));
     const int per_thread = nr >= 12 || nr == 0 ? 2 : (nr < 0 ? 1 : nr);
-    const int ahead = tile ? nr - 20 : (nr >= 12 ? nr - 10 : (nr < 0 ? -nr : 0));
+    const int ahead = tile ? nr - 19 : (nr >= 12 ? nr - 10 : (nr < 0 ? -nr : 0));
     const int block = tile ? 32 * gpb : kBlock;
     char buf[480];
     std::snprintf(buf, sizeof buf,

@@ -65,9 +65,9 @@ struct lqcd_server_s {
 
 namespace lqcd {
 
-static size_t request_bytes(const lqcd_lattice_s *lat, int prec)
+static size_t request_bytes(const lqcd_lattice_s *lat, int prec, bool twisted)
 {
-    return workspace_bytes(lat, 12, prec) + clover_bytes(lat) + sizeof(double) * lat->dims[3];
+    return workspace_bytes(lat, 12, prec) + clover_bytes(lat, twisted) + sizeof(double) * lat->dims[3];
 }
 
 static void run_request(lqcd_server_s *srv, ServeRequest *r, const ServeGauge &sg, cudaStream_t st)
@@ -76,7 +76,7 @@ static void run_request(lqcd_server_s *srv, ServeRequest *r, const ServeGauge &s
     GaugeSet &g = *sg.g;
     const int T = lat->dims[3];
     try {
-        auto cl = clover_build(lat, g, r->dp.kappa, r->dp.csw, st, true);
+        auto cl = clover_build(lat, g, r->dp, st, true);
         auto ws = workspace_build(lat, 12, r->sp.precision, st, true);
         DevBuf corr;
         corr.set_async(st);
@@ -233,8 +233,8 @@ int lqcd_serve_submit(lqcd_server srv, int gauge_id, const lqcd_dirac_params *dp
                       const int src[4], uint64_t *ticket)
 {
     if (!srv || !dp || !sp || !src || !ticket) return fail(LQCD_EINVAL, "null argument");
-    if (dp->mu != 0.0) return fail(LQCD_ENOTIMPL, "twisted mass mu != 0 is not supported");
-    if (!(dp->kappa >= 0.0) || !std::isfinite(dp->csw)) return fail(LQCD_EINVAL, "bad dirac params");
+    if (!(dp->kappa >= 0.0) || !std::isfinite(dp->csw) || !std::isfinite(dp->mu))
+        return fail(LQCD_EINVAL, "bad dirac params");
     if (!(sp->tol > 0.0 && sp->tol < 1.0) || sp->maxiter < 1 || sp->precision < LQCD_PREC_FP64 ||
         sp->precision > LQCD_PREC_MIXED_FP16 || sp->inner_tol < 0.0 || sp->inner_tol >= 1.0)
         return fail(LQCD_EINVAL, "bad solver params");
@@ -249,7 +249,7 @@ int lqcd_serve_submit(lqcd_server srv, int gauge_id, const lqcd_dirac_params *dp
     r->dp = *dp;
     r->sp = *sp;
     std::memcpy(r->src, src, sizeof r->src);
-    r->bytes = request_bytes(lat, sp->precision);
+    r->bytes = request_bytes(lat, sp->precision, dp->mu != 0.0);
     size_t resident = 0;
     for (const ServeGauge &g : srv->gauges) resident += g.bytes;
     if (resident + r->bytes > srv->budget)

@@ -169,7 +169,8 @@ struct Solver {
     cudaStream_t st;
     HopArgs<F64, F64, F64> h64;
     HopArgs<W, W, W> hw;
-    CloverField<F64> a64, ai64;
+    HopArgs<F32, F32, F32> h32;  // FP32 operator of the coarse reliable updates (mixed solvers)
+    CloverField<F64> a64, ai64, ci64;  // ci64: the C blocks of a twisted inverse
     CloverField<W> aw, aiw;
     SpinorField<F64> b_e, b_o, bhat, x_e, x_o, t64, w64;
     SpinorField<W> p, t, w, r, z;
@@ -199,6 +200,7 @@ struct Solver {
         S = ws.state.as<RhsState>();
         a64 = clover_field<F64>(cl, false, Sd);
         ai64 = clover_field<F64>(cl, true, Sd);
+        ci64 = clover_field_c<F64>(cl, Sd);
         aw = clover_field<W>(cl, false, Sd);
         aiw = clover_field<W>(cl, true, Sd);
         const int nt = ntiles_of(lat->vh);
@@ -210,22 +212,32 @@ struct Solver {
         h64.nrhs = nrhs;
         h64.ntiles = nt;
         h64.U = link_field<F64>(g, Sd);
-        for (int mu = 0; mu < 4; ++mu) {
-            h64.th_re[mu] = dp.theta_re[mu];
-            h64.th_im[mu] = dp.theta_im[mu];
-        }
+        hop_theta(dp, h64.th_re, h64.th_im);
         h64.red = red;
+        h64.tau = cl.tau;
+        h64.clov2 = ci64;
         hw = HopArgs<W, W, W>{};
         hw.g = lat->geom;
         hw.nrhs = nrhs;
         hw.ntiles = nt;
         hw.U = link_field<W>(g, Sd);
-        for (int mu = 0; mu < 4; ++mu) {
-            hw.th_re[mu] = dp.theta_re[mu];
-            hw.th_im[mu] = dp.theta_im[mu];
-        }
+        hop_theta(dp, hw.th_re, hw.th_im);
         hw.red = red;
+        hw.tau = cl.tau;
+        hw.clov2 = clover_field_c<W>(cl, Sd);
+        h32 = HopArgs<F32, F32, F32>{};
+        h32.g = lat->geom;
+        h32.nrhs = nrhs;
+        h32.ntiles = nt;
+        h32.U = link_field<F32>(g, Sd);
+        hop_theta(dp, h32.th_re, h32.th_im);
+        h32.red = red;
+        h32.tau = cl.tau;
+        a32 = clover_field<F32>(cl, false, Sd);
+        ai32 = clover_field<F32>(cl, true, Sd);
+        h32.clov2 = clover_field_c<F32>(cl, Sd);
     }
+    CloverField<F32> a32, ai32;
 
     // right-hand sides expected to pass each gate, from the last host poll
     // (launch accounting only; -1 when unknown)
@@ -253,7 +265,7 @@ struct Solver {
         launch_norm2_f64(q, b_e, st);
         q.red.op = RED_ADD;
         launch_norm2_f64(q, b_o, st);
-        launch_clover_apply<F64, F64>(lat->vh, nrhs, 1, ai64, b_o, t64, st);
+        launch_clover_apply<F64, F64>(lat->vh, nrhs, 1, ai64, b_o, t64, st, h64.tau, ci64);
         HopArgs<F64, F64, F64> a = h64;
         a.parity = 0;
         a.in = t64;
@@ -291,7 +303,56 @@ struct Solver {
         a.clov = a64;
         a.coef = -kappa;
         launch_hop(a, SELF_CLOV, false, false, st);
-        launch_r_replace<W>(gated(ST_UPDATE, RED_RHAT), bhat, w64, r, st);
+        launch_r_replace<W, F64>(gated(ST_UPDATE, RED_RHAT), bhat, w64, r, st);
+    }
+
+    // The same with Dhat x evaluated in FP32 storage and arithmetic, for the
+    // updates of RHS whose residual is still large: the recomputed residual
+    // carries an error of order 1e-7 |bhat|, far below its size, and the
+    // update never declares convergence (RED_RHAT_COARSE); the updates near
+    // tol and the final check stay FP64.  The FP32 fields live in the FP64
+    // scratch buffers t64 (x, then the intermediate) and w64 (Dhat x).
+    static constexpr double kCoarseMin = 1e-4;  // coarse while |r| / |b| >= this
+    void reliable_update_coarse()
+    {
+        launch_x_update<E>(gated(ST_UPDATE, RED_STORE), S, e, x_e, st);
+        const long Sd = lat->stride;
+        const size_t half = field_bytes<F32>(Sd, nrhs);
+        SpinorField<F32> x32{ws.t64.as<float4>(), nullptr, Sd};
+        SpinorField<F32> t32{reinterpret_cast<float4 *>(ws.t64.as<char>() + half), nullptr, Sd};
+        SpinorField<F32> w32{ws.w64.as<float4>(), nullptr, Sd};
+        launch_convert<F64, F32>(lat->vh, nrhs, x_e, x32, st);
+        HopArgs<F32, F32, F32> a = h32;
+        a.gate_st = S;
+        a.gate = ST_UPDATE;
+        a.nactive = hint_update;
+        a.parity = 1;
+        a.in = x32;
+        a.out = t32;
+        a.clov = ai32;
+        a.coef = kappa;
+        launch_hop(a, HOP_CLOV, false, false, st);
+        a.parity = 0;
+        a.in = t32;
+        a.self = x32;
+        a.out = w32;
+        a.clov = a32;
+        a.coef = -kappa;
+        launch_hop(a, SELF_CLOV, false, false, st);
+        launch_r_replace<W, F32>(gated(ST_UPDATE, RED_RHAT_COARSE), bhat, w32, r, st);
+    }
+
+    // every RHS asking for an update still has a large residual (host view after a poll)
+    bool coarse_ok() const
+    {
+        if (std::is_same<W, F64>::value) return false;
+        for (int j = 0; j < nrhs; ++j) {
+            const RhsState &q = ws.host_state[j];
+            if (q.status != ST_UPDATE) continue;
+            if (q.iter >= q.maxiter || !(q.rr == q.rr)) return false;
+            if (q.rr * q.scale * q.scale < kCoarseMin * kCoarseMin * q.bnorm2) return false;
+        }
+        return true;
     }
 
     // w = Dhat p (|w|^2 -> alpha); e += alpha p; r -= alpha w   [gate ACTIVE]
@@ -478,7 +539,12 @@ struct Solver {
                         finished = true;
                         break;
                     }
-                    if (any_status(ST_UPDATE)) reliable_update();
+                    if (any_status(ST_UPDATE)) {
+                        if (coarse_ok())
+                            reliable_update_coarse();
+                        else
+                            reliable_update();
+                    }
                 } else {
                     reliable_update();
                 }
@@ -594,7 +660,7 @@ static int solve_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, const lqc
 void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, const double *in, double *out,
                      bool dag, cudaStream_t st)
 {
-    CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
+    CloverSet &cl = clover_get(lat, g, dp, st);
     Workspace &ws = workspace<F64, F64>(lat, 1, LQCD_PREC_FP64, st);
     const long Sd = lat->stride;
     SpinorField<F64> ie = fld<F64>(ws.b_e, nullptr, Sd), io = fld<F64>(ws.b_o, nullptr, Sd);
@@ -605,11 +671,9 @@ void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
     a.nrhs = 1;
     a.ntiles = ntiles_of(lat->vh);
     a.U = link_field<F64>(g, Sd);
-    for (int mu = 0; mu < 4; ++mu) {
-        a.th_re[mu] = dp.theta_re[mu];
-        a.th_im[mu] = dp.theta_im[mu];
-    }
+    hop_theta(dp, a.th_re, a.th_im);
     a.clov = clover_field<F64>(cl, false, Sd);
+    a.tau = cl.tau;
     a.coef = -dp.kappa;
     // (D psi)_p = A_p psi_p - kappa H_{p,1-p} psi_{1-p} on both parities
     a.parity = 0;
@@ -642,7 +706,7 @@ static void schur_apply_prec(lqcd_lattice_s *lat, GaugeSet &g, CloverSet &cl, co
 void schur_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, int precision, const double *in,
                      double *out, int nrhs, int repeat, bool dag, cudaStream_t st)
 {
-    CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
+    CloverSet &cl = clover_get(lat, g, dp, st);
     switch (precision) {
     case LQCD_PREC_FP64: schur_apply_prec<F64, F64>(lat, g, cl, dp, precision, in, out, nrhs, repeat, dag, st); break;
     case LQCD_PREC_MIXED_FP32:
@@ -662,7 +726,7 @@ int solve(lqcd_lattice_s *lat, int gauge_id, const lqcd_dirac_params &dp, const 
     auto it = lat->gauges.find(gauge_id);
     if (it == lat->gauges.end()) throw Error{LQCD_EINVAL, "unknown gauge id"};
     GaugeSet &g = *it->second;
-    CloverSet &cl = clover_get(lat, g, dp.kappa, dp.csw, st);
+    CloverSet &cl = clover_get(lat, g, dp, st);
     switch (sp.precision) {
     case LQCD_PREC_FP64:
         return solve_prec<F64, F64>(lat, g, cl, dp, sp, b_dev, x_dev, src, nrhs, info, corr_dev, st, guess);
@@ -717,7 +781,7 @@ static int batch_t(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int
         auto it = b->lat->gauges.find(jobs[k].gauge_id);
         if (it == b->lat->gauges.end()) throw Error{LQCD_EINVAL, "unknown gauge id in batch job " + std::to_string(k)};
         GaugeSet &g = *it->second;
-        CloverSet &cl = clover_get(b->lat, g, jobs[k].dp.kappa, jobs[k].dp.csw, b->st);
+        CloverSet &cl = clover_get(b->lat, g, jobs[k].dp, b->st);
         b->ws = workspace_build(b->lat, 12, sp.precision, b->st, false);
         b->s = std::make_unique<Solver<W, E>>(b->lat, *b->ws, g, cl, jobs[k].dp, 12, b->st);
         point_sources(b->lat, jobs[k].src, b->s->b_e, b->s->b_o, b->st);

@@ -36,7 +36,8 @@ class LqcdError(RuntimeError):
 
 class DiracParams(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("csw", ctypes.c_double), ("theta_re", ctypes.c_double * 4),
-                ("theta_im", ctypes.c_double * 4), ("mu", ctypes.c_double)]
+                ("theta_im", ctypes.c_double * 4), ("mu", ctypes.c_double), ("cF", ctypes.c_double),
+                ("bc", ctypes.c_int)]
 
 
 class SolverParams(ctypes.Structure):
@@ -98,6 +99,11 @@ def load():
         "lqcd_meson_contract": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp],
         "lqcd_pion_corr_batch": [ctypes.POINTER(PionJob), ctypes.c_int, ctypes.POINTER(SolverParams), ctypes.c_int, vp],
         "lqcd_pion_contract_noalloc": [ip, vp, ctypes.c_int, vp, vp],
+        "lqcd_gauge_flow": [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp],
+        "lqcd_gauge_observables": [vp, ctypes.c_int, dp, dp, dp, dp, vp],
+        "lqcd_gauge_download": [vp, ctypes.c_int, vp, ctypes.c_int, vp],
+        "lqcd_boundary_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), vp, vp,
+                               vp, ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
         "lqcd_serve_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)],
         "lqcd_serve_gauge": [vp, ip, vp, ip],
         "lqcd_serve_submit": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), ip,
@@ -164,10 +170,16 @@ def _stream_of(t, stream):
     return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
-def dirac_params(kappa, csw, theta=DEFAULT_THETA, mu=0.0) -> DiracParams:
+BCS = {"periodic": 0, "open": 1}
+
+
+def dirac_params(kappa, csw, theta=DEFAULT_THETA, mu=0.0, cF=1.0, bc="periodic") -> DiracParams:
+    """DiracParam (kappa instead of m0): theta phase factors, twisted mass mu, boundary
+    coefficient cF and the time boundary ("periodic" or "open")."""
     th = np.asarray(theta, dtype=np.complex128)
     p = DiracParams()
-    p.kappa, p.csw, p.mu = float(kappa), float(csw), float(mu)
+    p.kappa, p.csw, p.mu, p.cF = float(kappa), float(csw), float(mu), float(cF)
+    p.bc = BCS[bc] if isinstance(bc, str) else int(bc)
     for k in range(4):
         p.theta_re[k] = th[k].real
         p.theta_im[k] = th[k].imag
@@ -304,6 +316,44 @@ def pion_corr(lat, gauge_id, params: DiracParams, solver: SolverParams, src, dim
                                prop.ctypes.data_as(ctypes.c_void_p) if prop is not None else None, info, 0, None)
     _check(rc, allow=(OK, ENOCONV))
     return corr, prop, [i.as_dict() for i in info], rc
+
+
+def gauge_flow(lat, gauge_id, eps, nsteps, stream=None):
+    """Wilson flow (RK3) of the resident field, in place: t = nsteps * eps."""
+    _check(load().lqcd_gauge_flow(lat, int(gauge_id), float(eps), int(nsteps), stream))
+
+
+def gauge_observables(lat, gauge_id, T):
+    """(plaquette average, Eplaq[T], Eclov[T], Q[T]) per-slice sums."""
+    plaq = ctypes.c_double(0)
+    Ep, Ec, Q = np.zeros(T), np.zeros(T), np.zeros(T)
+    dpp = ctypes.POINTER(ctypes.c_double)
+    _check(load().lqcd_gauge_observables(lat, int(gauge_id), ctypes.byref(plaq), Ep.ctypes.data_as(dpp),
+                                         Ec.ctypes.data_as(dpp), Q.ctypes.data_as(dpp), None))
+    return plaq.value, Ep, Ec, Q
+
+
+def gauge_download(lat, gauge_id, dims):
+    """The resident FP64 links, host layout U[t, z, y, x, mu, 3, 3]."""
+    lx, ly, lz, lt = dims
+    U = np.zeros((lt, lz, ly, lx, 4, 3, 3), dtype=np.complex128)
+    _check(load().lqcd_gauge_download(lat, int(gauge_id), U.ctypes.data_as(ctypes.c_void_p), 0, None))
+    return U
+
+
+def boundary_corr(lat, gauge_id, params: DiracParams, solver: SolverParams, dims, want_prop=False):
+    """Boundary-to-bulk f_P, f_A (host arrays) from the six P+ wall sources on slice 0.
+
+    Returns (fP, fA, H or None [6, T, Z, Y, X, 4, 3], infos, status)."""
+    lx, ly, lz, lt = dims
+    fP, fA = np.zeros(lt), np.zeros(lt)
+    H = np.zeros((6, lt, lz, ly, lx, 4, 3), dtype=np.complex128) if want_prop else None
+    info = (SolveInfo * 6)()
+    rc = load().lqcd_boundary_corr(lat, int(gauge_id), ctypes.byref(params), ctypes.byref(solver),
+                                   fP.ctypes.data_as(ctypes.c_void_p), fA.ctypes.data_as(ctypes.c_void_p),
+                                   H.ctypes.data_as(ctypes.c_void_p) if H is not None else None, info, 0, None)
+    _check(rc, allow=(OK, ENOCONV))
+    return fP, fA, H, [i.as_dict() for i in info], rc
 
 
 def pion_corr_batch(jobs, solver: SolverParams, chunk=0):

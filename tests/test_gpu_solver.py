@@ -203,8 +203,9 @@ def test_zero_source_and_bad_arguments(lq):
             lq.pion_corr(lat, gid, lq.dirac_params(0.12, 1.0), lq.solver_params(), (4, 0, 0, 0), dims=dims)
         assert e.value.code == lq.EINVAL
         with pytest.raises(lq.LqcdError) as e:
-            lq.cg_solve(lat, gid, lq.dirac_params(0.12, 1.0, mu=0.1), lq.solver_params(), np.zeros((4, 4, 4, 4, 4, 3)))
-        assert e.value.code == lq.ENOTIMPL
+            lq.cg_solve(lat, gid, lq.dirac_params(0.12, 1.0, mu=float("nan")), lq.solver_params(),
+                        np.zeros((4, 4, 4, 4, 4, 3)))
+        assert e.value.code == lq.EINVAL
         with pytest.raises(lq.LqcdError) as e:
             lq.cg_solve(lat, 99, lq.dirac_params(0.12, 1.0), lq.solver_params(), np.zeros((4, 4, 4, 4, 4, 3)))
         assert e.value.code == lq.EINVAL
