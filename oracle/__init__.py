@@ -72,6 +72,12 @@ def _load():
         lib.oracle_boundary_corr.restype = ctypes.c_int
         lib.oracle_gauge_obs.argtypes = [ip, dp, dp, dp, dp, dp]
         lib.oracle_wilson_flow.argtypes = [ip, dp, ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_hmc.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, ctypes.c_double, dp,
+                                   dp]
+        lib.oracle_hmc.restype = ctypes.c_int
+        lib.oracle_wilson_action.argtypes = [ip, dp, ctypes.c_double]
+        lib.oracle_wilson_action.restype = ctypes.c_double
+        lib.oracle_hmc_force.argtypes = [ip, dp, ctypes.c_double, ctypes.c_long, ctypes.c_int, dp]
         lib.oracle_pion.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -234,6 +240,33 @@ def wilson_flow(dims, U, eps, nsteps) -> np.ndarray:
     out = np.zeros_like(U)
     _load().oracle_wilson_flow(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), float(eps), int(nsteps),
                                _dp(out))
+    return out
+
+
+def hmc(dims, U, beta, eps, nsteps, mom, u):
+    """One leapfrog HMC trajectory; mom: momenta [T, Z, Y, X, mu, 8] (coordinates on i lambda_a / 2),
+    u: uniform in (0, 1).  Returns (accepted, dH, field after the trajectory or U if rejected)."""
+    U, d = _c128(U), _dims(dims)
+    m = np.ascontiguousarray(mom, dtype=np.float64)
+    assert m.size == 8 * 4 * int(np.prod(dims))
+    out = np.zeros_like(U)
+    dH = ctypes.c_double(0)
+    acc = _load().oracle_hmc(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), float(beta), float(eps),
+                             int(nsteps), _dp(m), float(u), _dp(out), ctypes.byref(dH))
+    return bool(acc), dH.value, out
+
+
+def wilson_action(dims, U, beta) -> float:
+    U, d = _c128(U), _dims(dims)
+    return _load().oracle_wilson_action(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), float(beta))
+
+
+def hmc_force(dims, U, beta, site, mu) -> np.ndarray:
+    """The HMC force F = -dS at the link (lexicographic site, mu), 3x3 complex."""
+    U, d = _c128(U), _dims(dims)
+    out = np.zeros((3, 3), dtype=np.complex128)
+    _load().oracle_hmc_force(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), float(beta), int(site), int(mu),
+                             _dp(out))
     return out
 
 

@@ -878,6 +878,112 @@ void oracle_wilson_flow(const int *L, const double *U, double eps, int nsteps, d
 }
 
 /* ------------------------------------------------------------------ */
+/* Quenched Hybrid Monte Carlo (Sec. 3.1, HMC! with leapfrog)           */
+/* ------------------------------------------------------------------ */
+
+/* The Wilson gauge action with beta = 2N / g0^2 (N = 3), c0 = 1:
+ *   S = (beta / 3) sum_x sum_{mu<nu} Re tr (1 - U_p(x)). */
+static double wilson_action(const int L[4], const double *U, double beta)
+{
+    const long V = volume_of(L);
+    double s = 0.0;
+    for (long x = 0; x < V; ++x)
+        for (int p = 0; p < 6; ++p) s += 3.0 - creal(trace3(plaquette_at(L, U, x, PLANE[p][0], PLANE[p][1])));
+    return beta / 3.0 * s;
+}
+
+/* Momentum of a link from its 8 real coordinates: P = sum_a pi_a i lambda_a / 2 */
+static mat3 momentum_of(const double *pi)
+{
+    mat3 P;
+    memset(&P, 0, sizeof P);
+    const double r3 = 1.0 / sqrt(3.0);
+    P.m[0][1] += 0.5 * I * pi[0];
+    P.m[1][0] += 0.5 * I * pi[0];
+    P.m[0][1] += 0.5 * pi[1];
+    P.m[1][0] -= 0.5 * pi[1];
+    P.m[0][0] += 0.5 * I * pi[2];
+    P.m[1][1] -= 0.5 * I * pi[2];
+    P.m[0][2] += 0.5 * I * pi[3];
+    P.m[2][0] += 0.5 * I * pi[3];
+    P.m[0][2] += 0.5 * pi[4];
+    P.m[2][0] -= 0.5 * pi[4];
+    P.m[1][2] += 0.5 * I * pi[5];
+    P.m[2][1] += 0.5 * I * pi[5];
+    P.m[1][2] += 0.5 * pi[6];
+    P.m[2][1] -= 0.5 * pi[6];
+    P.m[0][0] += 0.5 * I * r3 * pi[7];
+    P.m[1][1] += 0.5 * I * r3 * pi[7];
+    P.m[2][2] -= I * r3 * pi[7];
+    return P;
+}
+
+/* The HMC force F = -d S (Lie derivative, generators i lambda_a / 2): the
+ * Wilson action is beta / 6 times the action of the flow generator, so
+ * F = (beta / 6) Z with Z of flow_generator. */
+static mat3 hmc_force(const int L[4], const double *U, long x, int mu, double beta)
+{
+    return scale3(flow_generator(L, U, x, mu), beta / 6.0);
+}
+
+/* One trajectory of the quenched HMC (HMC! of Sec. 3.1) with the leapfrog
+ * integrator of nsteps steps of size eps:
+ *   P += eps/2 F(U);  [U = exp(eps P) U;  P += eps F(U)] x (nsteps - 1);
+ *   U = exp(eps P) U;  P += eps/2 F(U),
+ * H = -sum tr P^2 + S(U).  mom: the initial momenta as 8 reals per link
+ * [site][mu][a] (drawn by the caller); u: a uniform number in (0, 1): the
+ * trajectory is accepted when u < exp(-dH).  Uout receives the accepted
+ * field (the final one, or U when rejected); returns accepted (0 / 1). */
+int oracle_hmc(const int *L, const double *U, double beta, double eps, int nsteps, const double *mom, double u,
+               double *Uout, double *dH)
+{
+    const long V = volume_of(L), n = 72 * V;
+    double *W = malloc(sizeof(double) * n);
+    mat3 *P = malloc(sizeof(mat3) * 4 * V);
+    memcpy(W, U, sizeof(double) * n);
+    double K0 = 0.0;
+    for (long k = 0; k < 4 * V; ++k) {
+        P[k] = momentum_of(mom + 8 * k);
+        K0 -= creal(trace3(mul(P[k], P[k])));
+    }
+    const double H0 = K0 + wilson_action(L, W, beta);
+    for (int s = 0; s <= nsteps; ++s) {
+        /* momentum: half step at both ends, full steps between */
+        const double h = (s == 0 || s == nsteps) ? 0.5 * eps : eps;
+        mat3 *F = malloc(sizeof(mat3) * 4 * V);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) F[4 * x + mu] = hmc_force(L, W, x, mu, beta);
+        for (long k = 0; k < 4 * V; ++k) P[k] = add(P[k], scale3(F[k], h));
+        free(F);
+        if (s == nsteps) break;
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu)
+                store_link(W, x, mu, mul(expm3(scale3(P[4 * x + mu], eps)), link_at(W, x, mu)));
+    }
+    double K1 = 0.0;
+    for (long k = 0; k < 4 * V; ++k) K1 -= creal(trace3(mul(P[k], P[k])));
+    *dH = K1 + wilson_action(L, W, beta) - H0;
+    const int acc = u < exp(-*dH);
+    memcpy(Uout, acc ? W : U, sizeof(double) * n);
+    free(W);
+    free(P);
+    return acc;
+}
+
+/* The Wilson action and the force at one link (for the pins) */
+double oracle_wilson_action(const int *L, const double *U, double beta) { return wilson_action(L, U, beta); }
+
+void oracle_hmc_force(const int *L, const double *U, double beta, long x, int mu, double *F)
+{
+    mat3 f = hmc_force(L, U, x, mu, beta);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            F[2 * (3 * a + b)] = creal(f.m[a][b]);
+            F[2 * (3 * a + b) + 1] = cimag(f.m[a][b]);
+        }
+}
+
+/* ------------------------------------------------------------------ */
 /* Point-source propagator and pion correlator (Sec. 3.3, propagator!) */
 /* ------------------------------------------------------------------ */
 

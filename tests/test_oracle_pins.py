@@ -773,3 +773,77 @@ def test_flow_is_third_order_covariant_unitary_and_lowers_the_action():
     assert all(b < a for a, b in zip(S, S[1:]))
     assert abs(np.sum(oracle.gauge_obs(dims, _transform(U, g))[1]) - S[0]) < 1e-12 * S[0]
     del gd
+
+
+# --------------------------------------------------------------------------
+# quenched HMC
+# --------------------------------------------------------------------------
+
+def _generators():
+    return np.array([0.5j * lam for lam in inputs.gell_mann()])  # T^a = i lambda_a / 2, tr T^a T^b = -delta / 2
+
+
+def _moms(dims, seed):
+    n = 8 * 4 * int(np.prod(dims))
+    return inputs.normals(seed, 0, n).reshape(tuple(dims[::-1]) + (4, 8))
+
+
+def test_hmc_force_is_minus_the_lie_derivative_of_the_action():
+    """F = -sum_a T^a d_a S with d_a S = d/dh S(exp(h T^a) U_link) at h = 0,
+    by central differences of the action."""
+    from scipy.linalg import expm
+    dims, beta = (4, 2, 2, 4), 5.7
+    U = inputs.gauge_field(dims, 0.5, seed=81)
+    Tg = _generators()
+    for site, mu in [(0, 0), (5, 3), (13, 1)]:
+        t, r = divmod(site, dims[0] * dims[1] * dims[2])
+        z, r = divmod(r, dims[0] * dims[1])
+        y, x = divmod(r, dims[0])
+        h = 1e-5
+        d = []
+        for a in range(8):
+            vals = []
+            for sg in (+1, -1):
+                Up = U.copy()
+                Up[t, z, y, x, mu] = expm(sg * h * Tg[a]) @ U[t, z, y, x, mu]
+                vals.append(oracle.wilson_action(dims, Up, beta))
+            d.append((vals[0] - vals[1]) / (2 * h))
+        want = -np.einsum("a,aij->ij", np.array(d), Tg)
+        got = oracle.hmc_force(dims, U, beta, site, mu)
+        assert np.max(np.abs(got - want)) <= 1e-8 * np.max(np.abs(want)), (site, mu)
+
+
+def test_hmc_leapfrog_energy_violation_is_second_order_and_covariant():
+    dims, beta, tau = (4, 2, 2, 4), 5.7, 0.5
+    U = inputs.gauge_field(dims, 0.4, seed=82)
+    mom = _moms(dims, 83)
+    dHs = [oracle.hmc(dims, U, beta, tau / n, n, mom, 0.5)[1] for n in (8, 16, 32)]
+    for a, b in zip(dHs, dHs[1:]):
+        assert 3.3 < abs(a) / abs(b) < 4.7, dHs
+    # gauge covariance: (U^g, g P g^dag) evolves into (U'^g, ...) with the same dH
+    g = inputs.gauge_transform(dims, seed=84)
+    Tg = _generators()
+    P = np.einsum("...a,aij->...ij", mom, Tg)
+    gP = g[..., None, :, :] @ P @ np.conj(np.swapaxes(g, -1, -2))[..., None, :, :]
+    mom_g = -2 * np.einsum("aij,...ji->...a", Tg, gP).real
+    acc, dH, Uf = oracle.hmc(dims, U, beta, tau / 16, 16, mom, 1e-300)
+    acc_g, dH_g, Uf_g = oracle.hmc(dims, _transform(U, g), beta, tau / 16, 16, mom_g, 1e-300)
+    assert acc and acc_g
+    assert abs(dH - dH_g) < 1e-11
+    assert np.max(np.abs(Uf_g - _transform(Uf, g))) < 1e-12
+
+
+def test_hmc_trivial_cases_and_metropolis():
+    dims, beta = (2, 2, 2, 2), 6.0
+    U1 = inputs.unit_gauge_field(dims)
+    acc, dH, Uf = oracle.hmc(dims, U1, beta, 0.1, 5, np.zeros(tuple(dims[::-1]) + (4, 8)), 0.5)
+    assert acc and dH == 0.0 and np.array_equal(Uf, U1)
+    U = inputs.gauge_field(dims, 0.4, seed=85)
+    mom = _moms(dims, 86)
+    _, dH, Uf = oracle.hmc(dims, U, beta, 0.2, 4, mom, 1e-300)
+    p = np.exp(-dH)
+    acc_lo, _, U_lo = oracle.hmc(dims, U, beta, 0.2, 4, mom, 0.999999 * min(p, 1.0))
+    assert acc_lo and np.array_equal(U_lo, Uf)
+    if p < 1.0:
+        acc_hi, _, U_hi = oracle.hmc(dims, U, beta, 0.2, 4, mom, 1.000001 * p)
+        assert not acc_hi and np.array_equal(U_hi, U)
