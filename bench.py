@@ -67,11 +67,13 @@ HOP_BYTES_PER_RHS = {"hop_f16_hopclov": 104.0, "hop_f16_selfclov": 156.0}
 HOP_BYTES_SHARED = {"hop_f16_hopclov": 336.0, "hop_f16_selfclov": 336.0}
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
 # one ncu capture (24^3x48, 331776 sites per parity, staged paired kernel;
-# its summary is kept under profiles/): 509.2 MB for hopclov and 722.9 MB
+# its summary is kept under profiles/): 509.1 MB for hopclov and 722.3 MB
 # for selfclov.  Every operand is read once per site, so the traffic scales
-# with the sites of a launch.  Valid only for the kernel sources the capture
-# was taken on (digest below); otherwise the bench reports null.
-HOP_TRAFFIC = {"digest": "c8e35e9532ed53ac", "hop_f16_hopclov": 509.23e6 / 331776, "hop_f16_selfclov": 722.86e6 / 331776}
+# with the sites of a launch (the paired kernel the autotuner may pick for
+# hopclov moves the same bytes, 509.8 MB in the same capture setting).
+# Valid only for the kernel sources the capture was taken on (digest
+# below); otherwise the bench reports null.
+HOP_TRAFFIC = {"digest": "f85561fb0030f471", "hop_f16_hopclov": 509.10e6 / 331776, "hop_f16_selfclov": 722.35e6 / 331776}
 KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh", "hopp_inst.cuh", "hops.cuh"]
 
 
@@ -549,6 +551,33 @@ def c1_latency(lqcd, reps=20):
             "x_sites_rel_err": float(np.max(np.abs(got - want)) / np.max(np.abs(want)))}
 
 
+def flow_measure(lqcd, dims=(32, 32, 32, 32), eps=0.01, steps=5):
+    """Wilson flow (RK3, FP64) on a seeded field of the paper's L/a = 32
+    lattice: ms per step, timed with CUDA events, and the time to t = 10 at
+    eps = 0.01 (1000 steps) it implies, with the plaquette action density
+    before and after as a check that the field was smoothed."""
+    import torch
+    from paper_2503_16994_gb300 import inputs
+    U = inputs.gauge_field(dims, 0.4, seed=3, workers=None)
+    lat = lqcd.lattice_create(dims)
+    try:
+        gid = lqcd.gauge_upload(lat, U)
+        e0 = float(np.sum(lqcd.gauge_observables(lat, gid, dims[3])[1]))
+        lqcd.gauge_flow(lat, gid, eps, 1)  # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lqcd.gauge_flow(lat, gid, eps, steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        e1 = float(np.sum(lqcd.gauge_observables(lat, gid, dims[3])[1]))
+    finally:
+        lqcd.lattice_destroy(lat)
+    return {"lattice": list(dims), "eps": eps, "ms_per_step": ms, "t10_s_est": ms * 1000 / 1e3,
+            "E_plaq_sum_before_after": [e0, e1], "arithmetic": "FP64"}
+
+
 # ---------------------------------------------------------------------------
 # serving: a Poisson stream of propagator requests of mixed sizes
 # ---------------------------------------------------------------------------
@@ -825,6 +854,7 @@ def run_ours(args):
         c1 = small_config_measure(lqcd, "c1", ["fp64", "fp16"], reps=5)
         c1["single_source"] = c1_latency(lqcd)
     meson = None if (args.no_meson or rank != 0) else meson_measure(lqcd, dims)
+    flow = None if (args.no_flow or rank != 0) else flow_measure(lqcd)
     serving = None
     if args.serve_requests > 0 and rank == 0:
         hi = serving_measure(lqcd, args.serve_requests)
@@ -870,10 +900,12 @@ def run_ours(args):
                                                                      "batched_vs_sequential_mixed",
                                                                      "batched_vs_sequential_fp64_est")},
             "meson_ms": None if not meson else meson["ms"],
+            "flow_32c4": None if not flow else {k: flow[k] for k in ("ms_per_step", "t10_s_est")},
         }
         # the JSON line is kept short (rounded, summaries only); the full legs go to stderr
         print(json.dumps({"bench_details": {"kernels": per_kernel, "tuning": lqcd.tune_report(), "dslash": dslash,
                                             "c2": c2, "c1": c1, "serving": serving, "batched": batch, "meson": meson,
+                                            "flow": flow,
                                             "cpu_baseline": cpu, "fp64_gpu": fp64, "roofline_timed_over":
                                             f"{psteps} profiled steps after the timed region",
                                             "ms_per_step_profiled": ms_prof / psteps}}), file=sys.stderr)
@@ -933,6 +965,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-meson", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the 16^3x32 and 4^4 legs against the goldens")
+    ap.add_argument("--no-flow", action="store_true", help="skip the Wilson-flow timing on 32^4")
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="steps re-run with every launch timed, for the kernel split and the roofline")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
