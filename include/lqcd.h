@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define LQCD_ABI_VERSION 2
+#define LQCD_ABI_VERSION 3
 
 /* status codes */
 enum {
@@ -324,6 +324,23 @@ int lqcd_gauge_flow(lqcd_lattice lat, int gauge_id, double eps, int nsteps, void
 int lqcd_gauge_observables(lqcd_lattice lat, int gauge_id, double *plaq, double *Eplaq, double *Eclov, double *Q,
                            void *stream);
 
+/* One trajectory of the quenched Hybrid Monte Carlo (HMC! of Sec. 3.1) on a
+ * resident gauge field, in place, with the leapfrog integrator of nsteps
+ * steps of size eps, for the Wilson gauge action with beta = 2N / g0^2,
+ * read as S = (beta / 3) sum_x sum_{mu<nu} Re tr (1 - U_p(x)) (c0 = 1):
+ *   P += eps/2 F(U);  [U = exp(eps P) U;  P += eps F(U)] x (nsteps - 1);
+ *   U = exp(eps P) U;  P += eps/2 F(U),      F = -dS (Lie derivative),
+ * H = -sum tr P^2 + S.  mom: the initial momenta, host, 8 V 4 doubles
+ * [site][mu][a] = coordinates on the generators i lambda_a / 2 (standard
+ * Gell-Mann order), drawn by the caller (normal for the HMC).  u: a uniform
+ * number in (0, 1) drawn by the caller; the trajectory is accepted when
+ * u < exp(-dH), otherwise the links are restored.  *dH receives H(end) -
+ * H(start), *accepted 1 or 0.  FP64; the FP32/FP16 copies are rebuilt and
+ * the cached clover fields dropped.  Omelyan integrators and the c1 (1x2
+ * loop) terms of the paper's action are not built. */
+int lqcd_hmc_trajectory(lqcd_lattice lat, int gauge_id, double beta, double eps, int nsteps, const double *mom,
+                        double u, double *dH, int *accepted, void *stream);
+
 /* The resident FP64 links in the host layout of lqcd_gauge_upload (72 V
  * doubles; host memory, or device memory with LQCD_DEVICE_PTRS). */
 int lqcd_gauge_download(lqcd_lattice lat, int gauge_id, double *U, int flags, void *stream);
@@ -372,6 +389,25 @@ int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count);
  * force a shape instead.  Returns LQCD_EINVAL
  * if buf is too small (the text is truncated). */
 int lqcd_tune_report(char *buf, size_t len);
+
+/* The autotuner's decisions of this process (timed or imported) as text
+ * that lqcd_tune_import reads back, so that a later process (a restarted
+ * server) skips the timing: a header line "lqcd-tune 1", then one line per
+ * decision "<format> <mode> <sites per parity> <nrhs> <nr> <gpb> <minb> <swz>"
+ * (format f64, f32 or f16; mode 0 = t = kappa A^-1 H in, 1 = A self -
+ * kappa H in; nr the shape code of lqcd_tune_report, gpb its
+ * rhs_groups_per_block, minb min_blocks_per_sm, swz tiles_per_supertile).
+ * The shapes are valid on the GPU model that timed them.  Returns LQCD_EINVAL
+ * if buf is too small (the text is truncated). */
+int lqcd_tune_export(char *buf, size_t len);
+
+/* Loads decisions in the format of lqcd_tune_export: the first launch of a
+ * listed (format, mode, sites, nrhs) uses the shape without timing the
+ * candidates (reported with "source": "imported").  Every line is checked
+ * first (header, field count, a shape the launcher accepts for the format);
+ * on any error nothing is loaded and LQCD_EINVAL is returned.  Shapes already
+ * chosen in this process are kept.  Host-only: needs no GPU. */
+int lqcd_tune_import(const char *text);
 
 /* The pion contraction of lqcd_pion_contract without any device allocation,
  * for callers that cannot allocate: processes whose device memory belongs

@@ -200,6 +200,27 @@ int lqcd_gauge_observables(lqcd_lattice lat, int gauge_id, double *plaq, double 
     API_CATCH
 }
 
+int lqcd_hmc_trajectory(lqcd_lattice lat, int gauge_id, double beta, double eps, int nsteps, const double *mom,
+                        double u, double *dH, int *accepted, void *stream)
+{
+    if (!lat || !mom || !dH || !accepted) return fail(LQCD_EINVAL, "null argument");
+    if (!(beta > 0.0) || !std::isfinite(beta) || !(eps > 0.0) || !std::isfinite(eps) || nsteps < 1)
+        return fail(LQCD_EINVAL, "beta and eps must be > 0, nsteps >= 1");
+    if (!(u > 0.0 && u < 1.0)) return fail(LQCD_EINVAL, "u must be in (0, 1)");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(double) * 32 * (size_t)lat->V;
+    lat->staging.ensure(bytes);
+    LQCD_CUDA(cudaMemcpyAsync(lat->staging.p, mom, bytes, cudaMemcpyHostToDevice, st));
+    *accepted = hmc_trajectory(lat, *it->second, beta, eps, nsteps, lat->staging.as<const double>(), u, dH, st);
+    return LQCD_OK;
+    API_CATCH
+}
+
 int lqcd_gauge_download(lqcd_lattice lat, int gauge_id, double *U, int flags, void *stream)
 {
     if (!lat || !U) return fail(LQCD_EINVAL, "null argument");

@@ -95,10 +95,13 @@ void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, Spin
 }
 
 template <class W, class WI>
-void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<WI> w, SpinorField<W> r, cudaStream_t st)
+void launch_r_replace(const VecArgs &v, SpinorField<F64> src, SpinorField<WI> w, SpinorField<W> r,
+                      SpinorField<F64> save, bool w_scaled, cudaStream_t st)
 {
-    ProfScope prof("cg_r_replace", double(v.vh) * nact(v) * (192.0 + spinor_bytes<WI>() + spinor_bytes<W>()), st);
-    cg_r_replace<W, WI><<<grid_of(v), kBlock, 0, st>>>(v, bhat, w, r);
+    ProfScope prof("cg_r_replace",
+                   double(v.vh) * nact(v) * (192.0 + spinor_bytes<WI>() + spinor_bytes<W>() + (save.p ? 192.0 : 0.0)),
+                   st);
+    cg_r_replace<W, WI><<<grid_of(v), kBlock, 0, st>>>(v, src, w, r, save, w_scaled);
     LQCD_CHECK_LAUNCH();
 }
 
@@ -145,15 +148,15 @@ template void launch_p_update<F16>(const VecArgs &, const RhsState *, SpinorFiel
 template void launch_x_update<F64>(const VecArgs &, const RhsState *, SpinorField<F64>, SpinorField<F64>, cudaStream_t);
 template void launch_x_update<F32>(const VecArgs &, const RhsState *, SpinorField<F32>, SpinorField<F64>, cudaStream_t);
 template void launch_r_replace<F64, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F64>,
-                                         cudaStream_t);
+                                         SpinorField<F64>, bool, cudaStream_t);
 template void launch_r_replace<F32, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F32>,
-                                         cudaStream_t);
+                                         SpinorField<F64>, bool, cudaStream_t);
 template void launch_r_replace<F16, F64>(const VecArgs &, SpinorField<F64>, SpinorField<F64>, SpinorField<F16>,
-                                         cudaStream_t);
+                                         SpinorField<F64>, bool, cudaStream_t);
 template void launch_r_replace<F32, F32>(const VecArgs &, SpinorField<F64>, SpinorField<F32>, SpinorField<F32>,
-                                         cudaStream_t);
+                                         SpinorField<F64>, bool, cudaStream_t);
 template void launch_r_replace<F16, F32>(const VecArgs &, SpinorField<F64>, SpinorField<F32>, SpinorField<F16>,
-                                         cudaStream_t);
+                                         SpinorField<F64>, bool, cudaStream_t);
 template void launch_clover_apply<F64, F64>(long, int, int, CloverField<F64>, SpinorField<F64>, SpinorField<F64>,
                                             cudaStream_t, double, CloverField<F64>);
 

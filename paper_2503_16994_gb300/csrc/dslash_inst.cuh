@@ -9,14 +9,6 @@
 
 namespace lqcd {
 
-inline FastDiv make_fastdiv(unsigned d)
-{
-    unsigned l = 0;
-    while ((1ull << l) < d) ++l;
-    unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
-    return FastDiv{d, unsigned(m), l};
-}
-
 template <class S, int NR, int MODE, bool DAG, bool NORM>
 static void hopf_go(const FastHop<S> &f, cudaStream_t st)
 {
@@ -147,6 +139,17 @@ static HopShape hopf_tuned(FastHop<S> f, int mode, cudaStream_t st)
         std::lock_guard<std::mutex> lk(mu);
         auto it = table.find(key);
         if (it != table.end()) return it->second;
+    }
+    {
+        // a shape imported from an earlier process (lqcd_tune_import) is used as is
+        int sh[4];
+        if (tune_imported(prec_name<S>(), mode, f.vh, f.nrhs, sh)) {
+            const HopShape h{sh[0], sh[1], sh[2], sh[3]};
+            std::lock_guard<std::mutex> lk(mu);
+            if (table.emplace(key, h).second)
+                tune_record(prec_name<S>(), mode, f.vh, f.nrhs, h.nr, h.gpb, h.minb, h.swz, -1.f);
+            return table[key];
+        }
     }
     // one tuning at a time in the process (server slots may ask concurrently);
     // whoever waited finds the result in the table

@@ -139,15 +139,81 @@ __device__ m3 expm3(const m3 &X)
     return E;
 }
 
-// U_mu(x) <- exp(X_mu(x)) U_mu(x)
-__global__ void __launch_bounds__(128) flow_update_kernel(Geom g, double2 *u64, const double2 *X)
+// U_mu(x) <- exp(s X_mu(x)) U_mu(x)
+__global__ void __launch_bounds__(128) flow_update_kernel(Geom g, double2 *u64, const double2 *X, double s)
 {
     const long cb = long(blockIdx.x) * blockDim.x + threadIdx.x;
     const int p = blockIdx.y, mu = blockIdx.z;
     if (cb >= g.vh) return;
     double2 *ub = u64 + (long)(p * 4 + mu) * 9 * g.stride;
     const double2 *xb = X + (long)(p * 4 + mu) * 9 * g.stride;
-    store_m3(ub, g.stride, cb, mm(expm3(load_m3(xb, g.stride, cb)), load_m3(ub, g.stride, cb)));
+    m3 x = load_m3(xb, g.stride, cb);
+    if (s != 1.0)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) x.m[i][j] = s * x.m[i][j];
+    store_m3(ub, g.stride, cb, mm(expm3(x), load_m3(ub, g.stride, cb)));
+}
+
+// HMC momenta: P_mu(x) = sum_a pi_a i lambda_a / 2 from the caller's
+// coordinates pi (host layout [site][mu][8], on the device)
+__global__ void __launch_bounds__(128) momenta_kernel(Geom g, long V, const double *pi, double2 *P)
+{
+    const long s = long(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    long r = s;
+    int x[4];
+    x[0] = int(r % g.L[0]);
+    r /= g.L[0];
+    x[1] = int(r % g.L[1]);
+    r /= g.L[1];
+    x[2] = int(r % g.L[2]);
+    x[3] = int(r / g.L[2]);
+    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const long cb = s >> 1;
+    const double r3 = 0.57735026918962576451;  // 1 / sqrt 3
+    for (int mu = 0; mu < 4; ++mu) {
+        const double *a = pi + (s * 4 + mu) * 8;
+        m3 M;
+        // i lambda_1..8 / 2 weighted by a[0..7]
+        M.m[0][0] = cd{0.0, 0.5 * (a[2] + r3 * a[7])};
+        M.m[1][1] = cd{0.0, 0.5 * (-a[2] + r3 * a[7])};
+        M.m[2][2] = cd{0.0, -r3 * a[7]};
+        M.m[0][1] = cd{0.5 * a[1], 0.5 * a[0]};
+        M.m[1][0] = cd{-0.5 * a[1], 0.5 * a[0]};
+        M.m[0][2] = cd{0.5 * a[4], 0.5 * a[3]};
+        M.m[2][0] = cd{-0.5 * a[4], 0.5 * a[3]};
+        M.m[1][2] = cd{0.5 * a[6], 0.5 * a[5]};
+        M.m[2][1] = cd{-0.5 * a[6], 0.5 * a[5]};
+        store_m3(P + (long)(p * 4 + mu) * 9 * g.stride, g.stride, cb, M);
+    }
+}
+
+// partial[block] = sum over the block's links of -tr P^2 (one thread per link)
+__global__ void __launch_bounds__(128) kinetic_kernel(Geom g, const double2 *P, double *partial)
+{
+    __shared__ double sh[32];
+    const long cb = long(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;  // parity * 4 + mu
+    double v = 0.0;
+    if (cb < g.vh) {
+        const m3 M = load_m3(P + (long)q * 9 * g.stride, g.stride, cb);
+        const m3 MM = mm(M, M);
+        v = -(MM.m[0][0].re + MM.m[1][1].re + MM.m[2][2].re);
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
+}
+
+// out[0] = sum of the n partials in a fixed order (one block)
+__global__ void __launch_bounds__(512) sum_partials_kernel(const double *partial, long n, double *out)
+{
+    __shared__ double sh[32];
+    double t = 0.0;
+    for (long k = threadIdx.x; k < n; k += blockDim.x) t += partial[k];
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) out[0] = t;
 }
 
 // FP32 / FP16 reconstruct-12 copies from the FP64 links (after the flow)
@@ -272,7 +338,7 @@ void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaSt
                 LQCD_CHECK_LAUNCH();
             }
             ProfScope prof("flow_update", ubytes, st);
-            flow_update_kernel<<<gu, 128, 0, st>>>(lat->geom, u, X.as<const double2>());
+            flow_update_kernel<<<gu, 128, 0, st>>>(lat->geom, u, X.as<const double2>(), 1.0);
             LQCD_CHECK_LAUNCH();
         }
     const dim3 gr(unsigned((lat->vh + 127) / 128), 8);
@@ -281,6 +347,78 @@ void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaSt
     LQCD_CHECK_LAUNCH();
     LQCD_CUDA(cudaStreamSynchronize(st));  // X is freed on return
     g.clover.clear();                      // the clover fields belong to the old links
+}
+
+// S = (beta / 6) sum_t Eplaq[t] from the observables kernel (host value)
+static double wilson_action(lqcd_lattice_s *lat, GaugeSet &g, double beta, double *out_dev, cudaStream_t st)
+{
+    const int T = lat->dims[3];
+    gauge_observables(lat, g, out_dev, st);
+    std::vector<double> h(T);
+    LQCD_CUDA(cudaMemcpyAsync(h.data(), out_dev + T, sizeof(double) * T, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += h[t];
+    return beta / 6.0 * s;
+}
+
+static double kinetic_energy(lqcd_lattice_s *lat, const double2 *P, double *scratch, cudaStream_t st)
+{
+    const unsigned nb = unsigned((lat->vh + 127) / 128);
+    kinetic_kernel<<<dim3(nb, 8), 128, 0, st>>>(lat->geom, P, scratch);
+    LQCD_CHECK_LAUNCH();
+    sum_partials_kernel<<<1, 512, 0, st>>>(scratch, long(nb) * 8, scratch + long(nb) * 8);
+    LQCD_CHECK_LAUNCH();
+    double k = 0.0;
+    LQCD_CUDA(cudaMemcpyAsync(&k, scratch + long(nb) * 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    return k;
+}
+
+int hmc_trajectory(lqcd_lattice_s *lat, GaugeSet &g, double beta, double eps, int nsteps, const double *mom_dev,
+                   double u, double *dH, cudaStream_t st)
+{
+    const long S = lat->stride;
+    const int T = lat->dims[3];
+    const size_t ubytes = sizeof(double2) * 2 * 4 * 9 * S;
+    DevBuf P, backup, scratch;
+    P.ensure(ubytes);
+    backup.ensure(ubytes);
+    const unsigned nb = unsigned((lat->vh + 127) / 128);
+    scratch.ensure(sizeof(double) * std::max<size_t>(4 * T, size_t(nb) * 8 + 1));
+    double2 *u64 = g.u64.as<double2>();
+    LQCD_CUDA(cudaMemcpyAsync(backup.p, u64, ubytes, cudaMemcpyDeviceToDevice, st));
+    momenta_kernel<<<unsigned((lat->V + 127) / 128), 128, 0, st>>>(lat->geom, lat->V, mom_dev, P.as<double2>());
+    LQCD_CHECK_LAUNCH();
+    const double H0 = kinetic_energy(lat, P.as<const double2>(), scratch.as<double>(), st) +
+                      wilson_action(lat, g, beta, scratch.as<double>(), st);
+    const dim3 gf(unsigned((lat->vh + 63) / 64), 2, 4), gu(unsigned((lat->vh + 127) / 128), 2, 4);
+    const LinkField<F64> U{u64, nullptr, S};
+    const double fbytes = double(lat->V) * 4 * (8 * 144.0 + 144.0), lbytes = double(lat->V) * 4 * 3 * 144.0;
+    for (int s = 0; s <= nsteps; ++s) {
+        const double h = (s == 0 || s == nsteps) ? 0.5 * eps : eps;  // P += h F(U), F = (beta / 6) Z
+        {
+            ProfScope prof("hmc_force", fbytes, st);
+            flow_force_kernel<<<gf, 64, 0, st>>>(lat->geom, U, P.as<double2>(), h * beta / 6.0, 1.0);
+            LQCD_CHECK_LAUNCH();
+        }
+        if (s == nsteps) break;
+        ProfScope prof("hmc_links", lbytes, st);  // U = exp(eps P) U
+        flow_update_kernel<<<gu, 128, 0, st>>>(lat->geom, u64, P.as<const double2>(), eps);
+        LQCD_CHECK_LAUNCH();
+    }
+    const double H1 = kinetic_energy(lat, P.as<const double2>(), scratch.as<double>(), st) +
+                      wilson_action(lat, g, beta, scratch.as<double>(), st);
+    *dH = H1 - H0;
+    const bool acc = u < std::exp(-*dH);
+    if (!acc) LQCD_CUDA(cudaMemcpyAsync(u64, backup.p, ubytes, cudaMemcpyDeviceToDevice, st));
+    const dim3 gr(unsigned((lat->vh + 127) / 128), 8);
+    recon_copies_kernel<<<gr, 128, 0, st>>>(lat->geom, g.u64.as<const double2>(), g.u32.as<float4>(),
+                                            g.u16.as<uint4>(), g.u16b.as<uint2>());
+    LQCD_CHECK_LAUNCH();
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    g.clover.clear();
+    return acc ? 1 : 0;
 }
 
 void gauge_observables(lqcd_lattice_s *lat, GaugeSet &g, double *out_dev, cudaStream_t st)

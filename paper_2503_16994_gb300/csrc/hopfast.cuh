@@ -25,6 +25,14 @@ struct FastDiv {
 
 __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f) { return (__umulhi(n, f.m) + n) >> f.s; }
 
+inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{d, unsigned(m), l};
+}
+
 template <class S>
 struct FastHop {
     int L[4];

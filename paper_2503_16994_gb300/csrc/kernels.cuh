@@ -24,6 +24,7 @@ struct RhsState {
     double target2;  // stop when the FP64 residual norm^2 <= target2
     double delta2;   // reliable-update factor squared
     double acc;      // accumulator for norms (true residual, |b|^2)
+    double anchor2;  // |rhat|^2 of the last FP64 residual (the anchor of the incremental updates)
     int status;
     int iter;
     int updates;
@@ -39,7 +40,7 @@ enum RedOp : int {
     RED_BETA = 3,    // beta = sum / gamma (0 on the first pass); gamma = sum
     RED_RUPDATE = 4, // rr = sum; iter++; request an FP64 residual when due
     RED_RHAT = 5,    // sum = |FP64 residual|^2: finish, or resume the inner iteration
-    RED_RHAT_COARSE = 6  // sum = |residual|^2 recomputed with an FP32 operator: resume (never finishes)
+    RED_RHAT_COARSE = 6  // sum = |residual|^2 updated with an FP32 operator: resume (never finishes)
 };
 
 struct Reduce {
@@ -72,6 +73,7 @@ __device__ __forceinline__ void apply_op(const Reduce &r, int j, double sum)
         s.updates += 1;
         s.rr = sum / (s.scale * s.scale);
         s.rr_ref = s.rr;
+        s.anchor2 = sum;
         if (sum <= s.target2)
             s.status = ST_DONE;
         else if (s.iter >= s.maxiter || !(sum == sum))
@@ -399,18 +401,38 @@ __global__ void __launch_bounds__(128) cg_x_update(VecArgs v, const RhsState *st
     store_spinor<E, double>(e, j, i, z);
 }
 
-// rhat = bhat - w (FP64 arithmetic; w in FP64, or FP32 for a coarse
-// update); r = rhat / scale (low precision); |rhat|^2 -> RED_RHAT(_COARSE)
+// an FP64 spinor through the coherent path (a field the same launch also writes)
+__device__ __forceinline__ spinor<double> load_spinor_f64_rw(const SpinorField<F64> &f, int j, int i)
+{
+    spinor<double> a;
+    double *v = reinterpret_cast<double *>(&a);
+    const double2 *b = f.p + (long)j * 12 * f.stride + i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 w = b[k * f.stride];
+        v[2 * k] = w.x;
+        v[2 * k + 1] = w.y;
+    }
+    return a;
+}
+
+// rhat = src - c w (FP64 arithmetic): the FP64 update has src = bhat, w =
+// Dhat x in FP64 and c = 1; the incremental update has src = the previous
+// rhat, w = Dhat e in FP32 and c = scale (w_scaled).  r = rhat / scale (low
+// precision); |rhat|^2 -> RED_RHAT(_COARSE); save (if set, may be src): rhat
+// kept in FP64 for the next incremental update
 template <class W, class WI>
-__global__ void __launch_bounds__(128) cg_r_replace(VecArgs v, SpinorField<F64> bhat, SpinorField<WI> w,
-                                                    SpinorField<W> r)
+__global__ void __launch_bounds__(128) cg_r_replace(VecArgs v, SpinorField<F64> src, SpinorField<WI> w,
+                                                    SpinorField<W> r, SpinorField<F64> save, bool w_scaled)
 {
     const int j = blockIdx.x % v.nrhs, tile = blockIdx.x / v.nrhs;
     if (v.gate_st && v.gate_st[j].status != v.gate) return;
     const int i = tile * blockDim.x + threadIdx.x;
     double n2 = 0.0;
     if (i < v.vh) {
-        spinor<double> rh = axpy_sp(-1.0, load_spinor<WI, double>(w, j, i), load_spinor<F64, double>(bhat, j, i));
+        const double c = w_scaled ? v.red.st[j].scale : 1.0;
+        spinor<double> rh = axpy_sp(-c, load_spinor<WI, double>(w, j, i), load_spinor_f64_rw(src, j, i));
+        if (save.p) store_spinor<F64, double>(save, j, i, rh);
         n2 = norm2_sp(rh);
         const double inv = 1.0 / v.red.st[j].scale;
         using R = typename std::conditional<std::is_same<W, F64>::value, double, float>::type;

@@ -168,8 +168,12 @@ struct ProfScope {
     ~ProfScope();
 };
 
-// records an autotuning decision (reported by lqcd_tune_report)
+// records an autotuning decision (reported by lqcd_tune_report and
+// lqcd_tune_export); ms < 0: taken from an imported table, not timed
 void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, int minb, int swz, float ms);
+// a shape imported by lqcd_tune_import for (format, mode, sites per parity,
+// nrhs): shape = (nr, gpb, minb, swz); false when none was imported
+bool tune_imported(const char *prec, int mode, int vh, int nrhs, int shape[4]);
 
 // algorithmic bytes per site of one field in a storage format
 template <class S> constexpr double spinor_bytes() { return S::W == 2 ? 192.0 : (S::W == 4 ? 96.0 : 52.0); }
@@ -194,6 +198,10 @@ void hop_theta(const lqcd_dirac_params &dp, double th_re[4], double th_im[4]);
 void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaStream_t st);
 void gauge_observables(lqcd_lattice_s *lat, GaugeSet &g, double *out_dev, cudaStream_t st);
 void gauge_download(lqcd_lattice_s *lat, GaugeSet &g, double *U_dev, cudaStream_t st);
+// one leapfrog HMC trajectory of the resident links with the caller's momenta
+// (device, [site][mu][8]); returns accepted (1) or rejected (0, links restored)
+int hmc_trajectory(lqcd_lattice_s *lat, GaugeSet &g, double beta, double eps, int nsteps, const double *mom_dev,
+                   double u, double *dH, cudaStream_t st);
 
 // host-layout <-> even-odd SoA FP64 (field_ops.cu)
 void spinor_to_soa(lqcd_lattice_s *lat, const double *aos, int nrhs, SpinorField<F64> even, SpinorField<F64> odd,
@@ -230,8 +238,8 @@ void launch_p_update(const VecArgs &v, const RhsState *s, SpinorField<W> z, Spin
 template <class E>
 void launch_x_update(const VecArgs &v, const RhsState *s, SpinorField<E> e, SpinorField<F64> x, cudaStream_t st);
 template <class W, class WI>
-void launch_r_replace(const VecArgs &v, SpinorField<F64> bhat, SpinorField<WI> w, SpinorField<W> r,
-                      cudaStream_t st);
+void launch_r_replace(const VecArgs &v, SpinorField<F64> src, SpinorField<WI> w, SpinorField<W> r,
+                      SpinorField<F64> save, bool w_scaled, cudaStream_t st);
 void launch_norm2_f64(const VecArgs &v, SpinorField<F64> x, cudaStream_t st);
 // finishes the per-tile partials a hopping kernel wrote with reduce_partial
 // (quad: the FP32 32-site partials of the tile kernel in r.partial_f)

@@ -3,6 +3,10 @@
 // pair of CUDA events brackets each launch on its own stream and the elapsed
 // times are summed when the statistics are read.
 #include <algorithm>
+#include <array>
+#include <string>
+#include <tuple>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -85,7 +89,37 @@ ProfScope::~ProfScope()
 namespace {
 std::mutex g_tune_mu;
 std::string g_tune;  // JSON objects, comma separated
+struct Decision {
+    std::string prec;
+    int mode, vh, nrhs, nr, gpb, minb, swz;
+};
+std::vector<Decision> g_decisions;  // made or imported in this process, in order
+// imported shapes: (format, mode, sites per parity, nrhs) -> (nr, gpb, minb, swz)
+std::map<std::tuple<std::string, int, int, int>, std::array<int, 4>> g_imported;
+
+// a shape the launcher accepts for its storage format (the candidates of the tuner)
+bool shape_valid(const std::string &prec, int mode, int vh, int nrhs, int nr, int gpb, int minb, int swz)
+{
+    if ((mode != 0 && mode != 1) || vh <= 0 || nrhs < 1 || gpb < 1 || gpb > 12) return false;
+    if (minb != 1 && minb != 3 && minb != 4 && minb != 6) return false;
+    if (swz != 1 && swz != 8 && swz != 32) return false;
+    const bool tile = nr == 20 || nr == 21;
+    if (prec == "f64") return nr == 1 && (minb == 1 || minb == 6);
+    const bool common = (nr >= 0 && nr <= 3) || nr == -2 || nr == -4 || nr == -8;
+    if (prec == "f32") return common;
+    if (prec == "f16") return common || nr == 12 || nr == 13 || (tile && gpb <= 6);
+    return false;
+}
 }  // namespace
+
+bool tune_imported(const char *prec, int mode, int vh, int nrhs, int shape[4])
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_imported.find(std::make_tuple(std::string(prec), mode, vh, nrhs));
+    if (it == g_imported.end()) return false;
+    for (int k = 0; k < 4; ++k) shape[k] = it->second[k];
+    return true;
+}
 
 void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, int minb, int swz, float ms)
 {
@@ -106,11 +140,13 @@ void tune_record(const char *prec, int mode, int vh, int nrhs, int nr, int gpb, 
                   "{\"kernel\": \"hop_%s_%s\", \"sites\": %d, \"nrhs\": %d, \"variant\": \"%s\", "
                   "\"rhs_per_thread\": %d, \"directions_ahead\": %d, "
                   "\"rhs_groups_per_block\": %d, \"min_blocks_per_sm\": %d, \"tiles_per_supertile\": %d, "
-                  "\"block\": %d, \"us\": %.2f}",
-                  prec, modes[mode], vh, nrhs, variant, per_thread, ahead, gpb, minb, swz, block, ms * 1e3);
+                  "\"block\": %d, \"us\": %.2f, \"source\": \"%s\"}",
+                  prec, modes[mode], vh, nrhs, variant, per_thread, ahead, gpb, minb, swz, block,
+                  ms >= 0.f ? ms * 1e3 : 0.0, ms >= 0.f ? "timed" : "imported");
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (!g_tune.empty()) g_tune += ", ";
     g_tune += buf;
+    g_decisions.push_back(Decision{prec, mode, vh, nrhs, nr, gpb, minb, swz});
 }
 
 }  // namespace lqcd
@@ -140,6 +176,53 @@ int lqcd_tune_report(char *buf, size_t len)
     std::strncpy(buf, j.c_str(), len - 1);
     buf[len - 1] = 0;
     return j.size() < len ? LQCD_OK : LQCD_EINVAL;
+}
+
+int lqcd_tune_export(char *buf, size_t len)
+{
+    if (!buf || len == 0) return fail(LQCD_EINVAL, "null buffer");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string t = "lqcd-tune 1\n";
+    char line[160];
+    for (const Decision &d : g_decisions) {
+        std::snprintf(line, sizeof line, "%s %d %d %d %d %d %d %d\n", d.prec.c_str(), d.mode, d.vh, d.nrhs, d.nr,
+                      d.gpb, d.minb, d.swz);
+        t += line;
+    }
+    std::strncpy(buf, t.c_str(), len - 1);
+    buf[len - 1] = 0;
+    return t.size() < len ? LQCD_OK : fail(LQCD_EINVAL, "buffer too small");
+}
+
+int lqcd_tune_import(const char *text)
+{
+    if (!text) return fail(LQCD_EINVAL, "null text");
+    std::vector<std::pair<std::tuple<std::string, int, int, int>, std::array<int, 4>>> rows;
+    const char *p = text;
+    int lineno = 0;
+    while (*p) {
+        const char *e = std::strchr(p, '\n');
+        std::string line = e ? std::string(p, e - p) : std::string(p);
+        p = e ? e + 1 : p + line.size();
+        ++lineno;
+        if (line.find_first_not_of(" \t\r") == std::string::npos) continue;
+        if (lineno == 1) {
+            if (line.rfind("lqcd-tune 1", 0) != 0) return fail(LQCD_EINVAL, "tune import: header 'lqcd-tune 1' expected");
+            continue;
+        }
+        char prec[8] = {0};
+        int v[7];
+        char extra = 0;
+        const int n = std::sscanf(line.c_str(), "%7s %d %d %d %d %d %d %d %c", prec, &v[0], &v[1], &v[2], &v[3], &v[4],
+                                  &v[5], &v[6], &extra);
+        if (n != 8 || !shape_valid(prec, v[0], v[1], v[2], v[3], v[4], v[5], v[6]))
+            return fail(LQCD_EINVAL, "tune import: invalid line " + std::to_string(lineno));
+        rows.push_back({std::make_tuple(std::string(prec), v[0], v[1], v[2]), std::array<int, 4>{v[3], v[4], v[5], v[6]}});
+    }
+    if (lineno == 0) return fail(LQCD_EINVAL, "tune import: empty text");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &r : rows) g_imported[r.first] = r.second;
+    return LQCD_OK;
 }
 
 int lqcd_profile_read(lqcd_kernel_stat *out, int max, int *count)

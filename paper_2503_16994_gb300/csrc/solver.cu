@@ -16,9 +16,11 @@
 // commutes with g5).  The inner vectors are FP64, FP32 or FP16; every time the
 // inner residual has dropped by delta (or looks converged, or the iteration
 // cap is hit) the correction is added to the FP64 solution and the residual
-// is recomputed in FP64 (reliable update), keeping p.  Per-RHS scalars and
-// the state machine live on the device; the host only polls the states every
-// few iterations.
+// is recomputed in FP64 (reliable update), keeping p.  Mixed solvers whose
+// residual is still far from tol and from the last FP64 one instead move
+// the FP64 residual by the FP32 image of the correction (incremental update,
+// below).  Per-RHS scalars and the state machine live on the device; the host
+// only polls the states every few iterations.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -141,7 +143,7 @@ __global__ void init_state_kernel(RhsState *s, int nrhs, double tol2, double del
     q.maxiter = maxiter;
     q.status = q.bnorm2 > 0.0 ? ST_UPDATE : ST_DONE;
     q.gamma = q.alpha = q.beta = 0.0;
-    q.rr = q.rr_ref = 0.0;
+    q.rr = q.rr_ref = q.anchor2 = 0.0;
     q.iter = 0;
     q.updates = -1;  // the first FP64 residual (of the zero start) is not an update
     q.resume = resume;
@@ -169,7 +171,7 @@ struct Solver {
     cudaStream_t st;
     HopArgs<F64, F64, F64> h64;
     HopArgs<W, W, W> hw;
-    HopArgs<F32, F32, F32> h32;  // FP32 operator of the coarse reliable updates (mixed solvers)
+    HopArgs<F32, F32, F32> h32;  // FP32 operator of the incremental residual updates (mixed solvers)
     CloverField<F64> a64, ai64, ci64;  // ci64: the C blocks of a twisted inverse
     CloverField<W> aw, aiw;
     SpinorField<F64> b_e, b_o, bhat, x_e, x_o, t64, w64;
@@ -303,56 +305,76 @@ struct Solver {
         a.clov = a64;
         a.coef = -kappa;
         launch_hop(a, SELF_CLOV, false, false, st);
-        launch_r_replace<W, F64>(gated(ST_UPDATE, RED_RHAT), bhat, w64, r, st);
+        launch_r_replace<W, F64>(gated(ST_UPDATE, RED_RHAT), bhat, w64, r, x_o, false, st);
     }
 
-    // The same with Dhat x evaluated in FP32 storage and arithmetic, for the
-    // updates of RHS whose residual is still large: the recomputed residual
-    // carries an error of order 1e-7 |bhat|, far below its size, and the
-    // update never declares convergence (RED_RHAT_COARSE); the updates near
-    // tol and the final check stay FP64.  The FP32 fields live in the FP64
-    // scratch buffers t64 (x, then the intermediate) and w64 (Dhat x).
-    static constexpr double kCoarseMin = 1e-4;  // coarse while |r| / |b| >= this
-    void reliable_update_coarse()
+    // Incremental update (mixed solvers): the residual moves from the last
+    // recomputed rhat (FP64, kept in x_o, which holds nothing else until the
+    // odd solution is rebuilt at the end) by the correction gathered since:
+    //   rhat <- rhat - scale Dhat e,   x += scale e,   r = rhat / scale,
+    // with Dhat e evaluated by the tuned FP32 kernels straight from e (FP32).
+    // Each step adds an error of order 1e-7 |Dhat| |scale e|, i.e. a small
+    // multiple of 1e-7 of the residual it starts from, so the error since the
+    // last FP64 residual (the anchor) stays of order 1e-7 |anchor|.  It is
+    // used while every RHS asking for an update has |rhat| >= kTau |anchor|
+    // and >= kTolFactor tol |b|, and never declares convergence
+    // (RED_RHAT_COARSE); the updates that can finish and the final true
+    // residual are FP64.  t64 and w64 hold the FP32 intermediate and Dhat e.
+    static constexpr double kTau = 1e-4;
+    static constexpr double kTolFactor = 3.0;
+    void reliable_update_incremental()
     {
-        launch_x_update<E>(gated(ST_UPDATE, RED_STORE), S, e, x_e, st);
-        const long Sd = lat->stride;
-        const size_t half = field_bytes<F32>(Sd, nrhs);
-        SpinorField<F32> x32{ws.t64.as<float4>(), nullptr, Sd};
-        SpinorField<F32> t32{reinterpret_cast<float4 *>(ws.t64.as<char>() + half), nullptr, Sd};
-        SpinorField<F32> w32{ws.w64.as<float4>(), nullptr, Sd};
-        launch_convert<F64, F32>(lat->vh, nrhs, x_e, x32, st);
-        HopArgs<F32, F32, F32> a = h32;
-        a.gate_st = S;
-        a.gate = ST_UPDATE;
-        a.nactive = hint_update;
-        a.parity = 1;
-        a.in = x32;
-        a.out = t32;
-        a.clov = ai32;
-        a.coef = kappa;
-        launch_hop(a, HOP_CLOV, false, false, st);
-        a.parity = 0;
-        a.in = t32;
-        a.self = x32;
-        a.out = w32;
-        a.clov = a32;
-        a.coef = -kappa;
-        launch_hop(a, SELF_CLOV, false, false, st);
-        launch_r_replace<W, F32>(gated(ST_UPDATE, RED_RHAT_COARSE), bhat, w32, r, st);
+        if constexpr (std::is_same<E, F32>::value) {
+            const long Sd = lat->stride;
+            SpinorField<F32> t32{ws.t64.as<float4>(), nullptr, Sd};
+            SpinorField<F32> w32{ws.w64.as<float4>(), nullptr, Sd};
+            HopArgs<F32, F32, F32> a = h32;
+            a.gate_st = S;
+            a.gate = ST_UPDATE;
+            a.nactive = hint_update;
+            a.parity = 1;
+            a.in = e;
+            a.out = t32;
+            a.clov = ai32;
+            a.coef = kappa;
+            launch_hop(a, HOP_CLOV, false, false, st);
+            a.parity = 0;
+            a.in = t32;
+            a.self = e;
+            a.out = w32;
+            a.clov = a32;
+            a.coef = -kappa;
+            launch_hop(a, SELF_CLOV, false, false, st);
+            launch_x_update<E>(gated(ST_UPDATE, RED_STORE), S, e, x_e, st);
+            launch_r_replace<W, F32>(gated(ST_UPDATE, RED_RHAT_COARSE), x_o, w32, r, x_o, true, st);
+        } else {
+            reliable_update();
+        }
     }
 
-    // every RHS asking for an update still has a large residual (host view after a poll)
-    bool coarse_ok() const
+    // every RHS asking for an update allows the incremental one (host view after a poll)
+    bool incremental_ok() const
     {
-        if (std::is_same<W, F64>::value) return false;
+        if (!std::is_same<E, F32>::value) return false;
+        const double lim2 = kTolFactor * kTolFactor * tol_ * tol_;
         for (int j = 0; j < nrhs; ++j) {
             const RhsState &q = ws.host_state[j];
             if (q.status != ST_UPDATE) continue;
             if (q.iter >= q.maxiter || !(q.rr == q.rr)) return false;
-            if (q.rr * q.scale * q.scale < kCoarseMin * kCoarseMin * q.bnorm2) return false;
+            const double r2 = q.rr * q.scale * q.scale;
+            if (r2 < kTau * kTau * q.anchor2 || r2 < lim2 * q.bnorm2) return false;
         }
         return true;
+    }
+
+    // the cheapest residual recomputation every RHS asking for one allows
+    // (host view after a poll)
+    void update_best()
+    {
+        if (incremental_ok())
+            reliable_update_incremental();
+        else
+            reliable_update();
     }
 
     // w = Dhat p (|w|^2 -> alpha); e += alpha p; r -= alpha w   [gate ACTIVE]
@@ -513,7 +535,10 @@ struct Solver {
         delta_ = std::is_same<W, F64>::value ? 1e-30 : (sp.inner_tol > 0 ? sp.inner_tol : delta_default);
         tol_ = sp.tol;
         prepare(0.5 * tol_, delta_, sp.maxiter, guess);
-        reliable_update();
+        if (guess)
+            reliable_update();
+        else  // from x = 0 the first residual is bhat itself (x_e holds zeros)
+            launch_r_replace<W, F64>(gated(ST_UPDATE, RED_RHAT), bhat, x_e, r, x_o, false, st);
         half2();
     }
 
@@ -539,12 +564,7 @@ struct Solver {
                         finished = true;
                         break;
                     }
-                    if (any_status(ST_UPDATE)) {
-                        if (coarse_ok())
-                            reliable_update_coarse();
-                        else
-                            reliable_update();
-                    }
+                    if (any_status(ST_UPDATE)) update_best();
                 } else {
                     reliable_update();
                 }
@@ -792,7 +812,7 @@ static int batch_t(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int
     for (auto &b : J) {
         b->s->half1();
         b->s->pull_states();
-        if (b->s->any_status(ST_UPDATE)) b->s->reliable_update();
+        if (b->s->any_status(ST_UPDATE)) b->s->update_best();
         b->s->half2();
     }
     for (auto &b : J) {
@@ -848,7 +868,7 @@ static int batch_t(lqcd_pion_job *jobs, int n, const lqcd_solver_params &sp, int
                 if (!b->active) continue;
                 b->s->pull_states();
                 if (b->s->any_status(ST_UPDATE)) {
-                    b->s->reliable_update();
+                    b->s->update_best();
                     b->s->resumed_to_active();
                 }
             }

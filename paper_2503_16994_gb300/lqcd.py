@@ -102,6 +102,8 @@ def load():
         "lqcd_gauge_flow": [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp],
         "lqcd_gauge_observables": [vp, ctypes.c_int, dp, dp, dp, dp, vp],
         "lqcd_gauge_download": [vp, ctypes.c_int, vp, ctypes.c_int, vp],
+        "lqcd_hmc_trajectory": [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp,
+                                ctypes.c_double, dp, ip, vp],
         "lqcd_boundary_corr": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), ctypes.POINTER(SolverParams), vp, vp,
                                vp, ctypes.POINTER(SolveInfo), ctypes.c_int, vp],
         "lqcd_serve_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)],
@@ -112,6 +114,8 @@ def load():
         "lqcd_serve_destroy": [vp],
         "lqcd_profile_reset": [ctypes.c_int],
         "lqcd_tune_report": [ctypes.c_char_p, ctypes.c_size_t],
+        "lqcd_tune_export": [ctypes.c_char_p, ctypes.c_size_t],
+        "lqcd_tune_import": [ctypes.c_char_p],
         "lqcd_profile_read": [ctypes.POINTER(KernelStat), ctypes.c_int, ip],
     }
     for name, args in sig.items():
@@ -333,6 +337,18 @@ def gauge_observables(lat, gauge_id, T):
     return plaq.value, Ep, Ec, Q
 
 
+def hmc_trajectory(lat, gauge_id, beta, eps, nsteps, mom, u):
+    """One leapfrog HMC trajectory of the resident field; mom [T, Z, Y, X, 4, 8] (coordinates on
+    i lambda_a / 2), u uniform in (0, 1).  Returns (accepted, dH)."""
+    m = np.ascontiguousarray(mom, dtype=np.float64)
+    dH = ctypes.c_double(0)
+    acc = ctypes.c_int(0)
+    _check(load().lqcd_hmc_trajectory(lat, int(gauge_id), float(beta), float(eps), int(nsteps),
+                                      m.ctypes.data_as(ctypes.c_void_p), float(u), ctypes.byref(dH),
+                                      ctypes.byref(acc), None))
+    return bool(acc.value), dH.value
+
+
 def gauge_download(lat, gauge_id, dims):
     """The resident FP64 links, host layout U[t, z, y, x, mu, 3, 3]."""
     lx, ly, lz, lt = dims
@@ -446,6 +462,18 @@ def profile_read() -> dict:
     return {buf[i].name.decode(): {"launches": buf[i].launches, "bytes": buf[i].bytes,
                                    "timed_launches": buf[i].timed_launches, "timed_ms": buf[i].timed_ms,
                                    "timed_bytes": buf[i].timed_bytes} for i in range(n.value)}
+
+
+def tune_export() -> str:
+    """The autotuner's decisions as text for tune_import (lqcd_tune_export)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().lqcd_tune_export(buf, len(buf)))
+    return buf.value.decode()
+
+
+def tune_import(text: str) -> None:
+    """Loads decisions written by tune_export (lqcd_tune_import)."""
+    _check(load().lqcd_tune_import(text.encode()))
 
 
 def tune_report() -> list:

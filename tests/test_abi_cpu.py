@@ -37,7 +37,7 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lqcd.abi_version() == 2
+    assert lqcd.abi_version() == 3
 
 
 @pytest.mark.parametrize("dims", [(3, 4, 4, 4), (4, 4, 4, 5), (0, 4, 4, 4), (4, 4, -2, 4)])
@@ -72,3 +72,32 @@ def test_no_device_is_an_error_not_a_crash(lib):
     with pytest.raises(lqcd.LqcdError) as e:
         lqcd.lattice_create((4, 4, 4, 4), device=0)
     assert e.value.code == lqcd.ECUDA
+
+
+def test_tune_import_validates_before_loading(lib):
+    # host-only: the tuner's table of shapes is read and checked without a GPU
+    good = "lqcd-tune 1\nf16 0 331776 12 12 3 3 1\nf16 1 331776 12 0 2 4 8\nf64 0 331776 12 1 2 1 1\n"
+    bad = [
+        "f16 0 331776 12 12 3 3 1\n",                       # no header
+        "lqcd-tune 2\nf16 0 331776 12 12 3 3 1\n",           # unknown version
+        "lqcd-tune 1\nf16 0 331776 12 12 3 3\n",             # a field missing
+        "lqcd-tune 1\nf16 0 331776 12 12 3 3 1 7\n",         # a field too many
+        "lqcd-tune 1\nf64 0 331776 12 0 2 3 1\n",            # paired shape for FP64
+        "lqcd-tune 1\nf32 1 331776 12 12 3 3 1\n",           # staged shape for FP32
+        "lqcd-tune 1\nf16 2 331776 12 1 1 1 1\n",            # no such mode
+        "lqcd-tune 1\nf16 0 331776 12 21 9 3 1\n",           # tile kernel with 9 pairs per block
+        "lqcd-tune 1\nf16 0 331776 12 1 1 5 1\n",            # no such register cap
+        "lqcd-tune 1\nbf16 0 331776 12 1 1 1 1\n",           # unknown format
+        good + "f16 0 -4 12 1 1 1 1\n",                      # one bad line spoils the whole text
+    ]
+    before = lqcd.tune_export()
+    assert before.startswith("lqcd-tune 1\n")
+    for text in bad:
+        with pytest.raises(lqcd.LqcdError) as e:
+            lqcd.tune_import(text)
+        assert e.value.code == lqcd.EINVAL, text
+    assert lqcd.tune_export() == before  # nothing was loaded
+    lqcd.tune_import(good)
+    # imported shapes are used (and reported) on the first launch of their key only
+    assert lqcd.tune_export() == before
+    assert lib.lqcd_tune_import(None) == lqcd.EINVAL
