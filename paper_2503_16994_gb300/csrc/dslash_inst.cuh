@@ -24,6 +24,21 @@ static void hopf_go(const FastHop<S> &f, cudaStream_t st)
 template <class S, int NR>
 static void hopf_dispatch(const FastHop<S> &f, int mode, bool dag, bool norm, cudaStream_t st)
 {
+    if constexpr (std::is_same<S, F64>::value) {
+        // the FP64 set-up and final modes of the solver (no dagger)
+        if (mode == SELF_PLAIN) {
+            norm ? hopf_go<S, NR, SELF_PLAIN, false, true>(f, st) : hopf_go<S, NR, SELF_PLAIN, false, false>(f, st);
+            return;
+        }
+        if (mode == CLOV_SUM) {
+            norm ? hopf_go<S, NR, CLOV_SUM, false, true>(f, st) : hopf_go<S, NR, CLOV_SUM, false, false>(f, st);
+            return;
+        }
+        if (mode == RESID) {
+            norm ? hopf_go<S, NR, RESID, false, true>(f, st) : hopf_go<S, NR, RESID, false, false>(f, st);
+            return;
+        }
+    }
     if (mode == HOP_CLOV) {
         if (dag) norm ? hopf_go<S, NR, HOP_CLOV, true, true>(f, st) : hopf_go<S, NR, HOP_CLOV, true, false>(f, st);
         else norm ? hopf_go<S, NR, HOP_CLOV, false, true>(f, st) : hopf_go<S, NR, HOP_CLOV, false, false>(f, st);
@@ -262,6 +277,7 @@ static FastHop<S> make_fast(const HopArgs<S, S, S> &a)
     f.in = a.in;
     f.self = a.self;
     f.out = a.out;
+    f.b = a.b;
     f.U = a.U;
     f.clov = a.clov;
     f.gate_st = a.gate_st;
@@ -308,8 +324,10 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
     const bool twinv = a.tau != 0.0 && (mode == HOP_CLOV || mode == CLOV_SUM);
     double shared = 8.0 * link_bytes<L>() + (mode == SELF_PLAIN ? 0.0 : (twinv ? 2.0 : 1.0) * clover_bytes<C>());
     const int pi = S::W == 2 ? 0 : (S::W == 4 ? 1 : 2);
-    // twisted mass runs on the generic kernel (hop_kernel) in every storage format
-    if ((mode == HOP_CLOV || mode == SELF_CLOV) && a.tau == 0.0) {
+    // twisted mass runs on the generic kernel (hop_kernel) in every storage
+    // format; the set-up and final modes have the fast kernel in FP64, without dagger
+    const bool extra = std::is_same<S, F64>::value && !dag && (mode == SELF_PLAIN || mode == CLOV_SUM || mode == RESID);
+    if ((mode == HOP_CLOV || mode == SELF_CLOV || extra) && (a.tau == 0.0 || mode == SELF_PLAIN)) {
         FastHop<S> f = make_fast(a);
         const HopShape sh = hopf_tuned<S>(f, mode, st);
         f.gpb = sh.gpb;

@@ -45,7 +45,7 @@ struct FastHop {
     int minb;                    // register cap: minimum resident blocks per SM (1, 4 or 6)
     int swz;                     // tiles per super-tile in the block order (1: tile-major)
     int theta_mask;              // bit mu set: theta_mu != 1
-    SpinorField<S> in, self, out;
+    SpinorField<S> in, self, out, b;  // b: RESID only
     LinkField<S> U;
     CloverField<S> clov;
     const RhsState *gate_st;
@@ -645,7 +645,28 @@ __device__ __forceinline__ void hopf_group(const FastHop<S> &a, int tile, int g)
         double n2 = 0.0;
         if (valid) {
             R res[24];
-            if constexpr (MODE == HOP_CLOV) {
+            if constexpr (MODE == SELF_PLAIN || MODE == CLOV_SUM) {
+                // self + coef H in, then (CLOV_SUM) times C
+                R sv[24];
+                const R sc = load_raw<S, R>(a.self, jj[r], i, sv);
+                if constexpr (S::W == 8) {
+#pragma unroll
+                    for (int q = 0; q < 24; ++q) sv[q] *= sc;
+                }
+#pragma unroll
+                for (int q = 0; q < 24; ++q) sv[q] = fma(coef, acc[r][q], sv[q]);
+                if constexpr (MODE == SELF_PLAIN) {
+#pragma unroll
+                    for (int q = 0; q < 24; ++q) res[q] = sv[q];
+                } else {
+                    R A[36];
+#pragma unroll
+                    for (int blk = 0; blk < 2; ++blk) {
+                        load_clov_block<S, R>(a.clov, a.parity, i, blk, A);
+                        clov6(A, sv + 12 * blk, res + 12 * blk);
+                    }
+                }
+            } else if constexpr (MODE == HOP_CLOV) {
                 // out = coef * C (H in)
                 R A[36];
 #pragma unroll
@@ -672,7 +693,20 @@ __device__ __forceinline__ void hopf_group(const FastHop<S> &a, int tile, int g)
 #pragma unroll
                 for (int q = 0; q < 24; ++q) res[q] = fma(coef, acc[r][q], res[q]);
             }
-            n2 = store_raw<S, R>(a.out, jj[r], i, res);
+            if constexpr (MODE == RESID) {
+                // |b - (C self + coef H in)|^2, nothing stored
+                R bv[24];
+                const R sb = load_raw<S, R>(a.b, jj[r], i, bv);
+                R t = R(0);
+#pragma unroll
+                for (int q = 0; q < 24; ++q) {
+                    const R d = bv[q] * sb - res[q];
+                    t = fma(d, d, t);
+                }
+                n2 = double(t);
+            } else {
+                n2 = store_raw<S, R>(a.out, jj[r], i, res);
+            }
         }
         if (NORM) {
             if constexpr (S::W == 2) reduce_partial<double>(a.red, jj[r], tile, a.ntiles, n2);
