@@ -72,6 +72,8 @@ def _load():
         lib.oracle_boundary_corr.restype = ctypes.c_int
         lib.oracle_gauge_obs.argtypes = [ip, dp, dp, dp, dp, dp]
         lib.oracle_wilson_flow.argtypes = [ip, dp, ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_laplacian.argtypes = [ip, dp, dp, dp, dp]
+        lib.oracle_fermion_flow.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, dp, dp]
         lib.oracle_hmc.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, ctypes.c_double, dp,
                                    dp]
         lib.oracle_hmc.restype = ctypes.c_int
@@ -241,6 +243,25 @@ def wilson_flow(dims, U, eps, nsteps) -> np.ndarray:
     _load().oracle_wilson_flow(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), float(eps), int(nsteps),
                                _dp(out))
     return out
+
+
+def laplacian(dims, U, psi, theta=DEFAULT_THETA) -> np.ndarray:
+    """Covariant Laplacian (Delta psi)(x) = sum_mu [U~ psi(x+mu) + U~^dag psi(x-mu) - 2 psi(x)], colour only."""
+    U, psi, th, d = _c128(U), _c128(psi), _theta(theta), _dims(dims)
+    out = np.zeros_like(psi)
+    _load().oracle_laplacian(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), _dp(th), _dp(psi), _dp(out))
+    return out
+
+
+def fermion_flow(dims, U, chi, eps, nsteps, theta=DEFAULT_THETA, nrhs=1):
+    """Gauge and quark fields after nsteps RK3 steps of the coupled Wilson / fermion flow.
+    chi: nrhs fields [nrhs, T, Z, Y, X, 4, 3] (or one field).  Returns (U_flowed, chi_flowed)."""
+    U, chi, th, d = _c128(U), _c128(chi), _theta(theta), _dims(dims)
+    assert chi.size == nrhs * 12 * int(np.prod(dims))
+    Uo, co = np.zeros_like(U), np.zeros_like(chi)
+    _load().oracle_fermion_flow(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), _dp(th), float(eps),
+                                int(nsteps), _dp(chi), int(nrhs), _dp(Uo), _dp(co))
+    return Uo, co
 
 
 def hmc(dims, U, beta, eps, nsteps, mom, u):

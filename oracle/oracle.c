@@ -877,6 +877,123 @@ void oracle_wilson_flow(const int *L, const double *U, double eps, int nsteps, d
     free(Z2);
 }
 
+/* Covariant lattice Laplacian on a quark field, the generator of the
+ * fermion gradient flow (Sec. 3.2, "Gradient flow for fermion fields
+ * following the lines of" Luescher, JHEP 2013):
+ *   (Delta psi)(x) = sum_mu [ U~_mu(x) psi(x+mu) + U~_mu(x-mu)^dag psi(x-mu)
+ *                             - 2 psi(x) ],
+ * acting on colour only (the identity in spin), with the boundary phases
+ * theta of the Dirac operator on the links that leave the last slice. */
+static void laplacian(const int L[4], const double *U, const cplx th[4], const double *in, double *out)
+{
+    const long V = volume_of(L);
+    for (long x = 0; x < V; ++x) {
+        int xc[4];
+        coords_of(L, x, xc);
+        spinor acc = spinor_at(in, x);
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) acc.c[al][a] *= -8.0;
+        for (int mu = 0; mu < 4; ++mu) {
+            long y = step(L, x, mu, +1);
+            cplx ph = (xc[mu] == L[mu] - 1) ? th[mu] : 1.0;
+            spinor v = colour_mul(link_at(U, x, mu), ph, spinor_at(in, y));
+            y = step(L, x, mu, -1);
+            ph = (xc[mu] == 0) ? conj(th[mu]) : 1.0;
+            spinor w = colour_mul(dag(link_at(U, y, mu)), ph, spinor_at(in, y));
+            for (int al = 0; al < 4; ++al)
+                for (int a = 0; a < 3; ++a) acc.c[al][a] += v.c[al][a] + w.c[al][a];
+        }
+        spinor_store(out, x, &acc);
+    }
+}
+
+void oracle_laplacian(const int *L, const double *U, const double *theta, const double *in, double *out)
+{
+    cplx th[4];
+    for (int mu = 0; mu < 4; ++mu) th[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
+    laplacian(L, U, th, in, out);
+}
+
+/* out = a x + b y (n doubles) */
+static void axpby(long n, double a, const double *x, double b, const double *y, double *out)
+{
+    for (long k = 0; k < n; ++k) out[k] = a * x[k] + b * y[k];
+}
+
+/* Fermion gradient flow (Sec. 3.2): d chi / dt = Delta(V_t) chi with the gauge
+ * field flowed alongside by the Wilson flow of oracle_wilson_flow.  Reading:
+ * Luescher's third-order scheme for the pair, the fermion stages evaluated on
+ * the gauge stages W0 = V_t, W1, W2 of the same step:
+ *   lambda1 = chi + (1/4) eps Delta(W0) chi,
+ *   lambda2 = chi + (8/9) eps Delta(W1) lambda1 - (2/9) eps Delta(W0) chi,
+ *   chi(t + eps) = lambda1 + (3/4) eps Delta(W2) lambda2
+ * (Butcher weights c = (0, 1/4, 2/3), b = (1/4, 0, 3/4): third order).
+ * nrhs quark fields chi[nrhs][site][spin][colour]; U, chi in; Uout, chiout
+ * out (chiout may alias chi, Uout may alias U). */
+void oracle_fermion_flow(const int *L, const double *U, const double *theta, double eps, int nsteps,
+                         const double *chi, int nrhs, double *Uout, double *chiout)
+{
+    const long V = volume_of(L), n = 72 * V, f = 24 * V;
+    cplx th[4];
+    for (int mu = 0; mu < 4; ++mu) th[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
+    double *W = malloc(sizeof(double) * n);
+    double *c = malloc(sizeof(double) * f * nrhs), *d0 = malloc(sizeof(double) * f * nrhs);
+    double *l1 = malloc(sizeof(double) * f * nrhs), *l2 = malloc(sizeof(double) * f * nrhs);
+    double *tmp = malloc(sizeof(double) * f);
+    mat3 *Z0 = malloc(sizeof(mat3) * 4 * V), *Z1 = malloc(sizeof(mat3) * 4 * V), *Z2 = malloc(sizeof(mat3) * 4 * V);
+    memcpy(W, U, sizeof(double) * n);
+    memcpy(c, chi, sizeof(double) * f * nrhs);
+    for (int k = 0; k < nsteps; ++k) {
+        /* W0 */
+        for (int j = 0; j < nrhs; ++j) {
+            laplacian(L, W, th, c + f * j, d0 + f * j);
+            axpby(f, 1.0, c + f * j, 0.25 * eps, d0 + f * j, l1 + f * j);
+        }
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) Z0[4 * x + mu] = scale3(flow_generator(L, W, x, mu), eps);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu)
+                store_link(W, x, mu, mul(expm3(scale3(Z0[4 * x + mu], 0.25)), link_at(W, x, mu)));
+        /* W1 */
+        for (int j = 0; j < nrhs; ++j) {
+            laplacian(L, W, th, l1 + f * j, tmp);
+            axpby(f, 1.0, c + f * j, 8.0 / 9.0 * eps, tmp, l2 + f * j);
+            axpby(f, 1.0, l2 + f * j, -2.0 / 9.0 * eps, d0 + f * j, l2 + f * j);
+        }
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) Z1[4 * x + mu] = scale3(flow_generator(L, W, x, mu), eps);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) {
+                mat3 X = add(scale3(Z1[4 * x + mu], 8.0 / 9.0), scale3(Z0[4 * x + mu], -17.0 / 36.0));
+                store_link(W, x, mu, mul(expm3(X), link_at(W, x, mu)));
+            }
+        /* W2 */
+        for (int j = 0; j < nrhs; ++j) {
+            laplacian(L, W, th, l2 + f * j, tmp);
+            axpby(f, 1.0, l1 + f * j, 0.75 * eps, tmp, c + f * j);
+        }
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) Z2[4 * x + mu] = scale3(flow_generator(L, W, x, mu), eps);
+        for (long x = 0; x < V; ++x)
+            for (int mu = 0; mu < 4; ++mu) {
+                mat3 X = add(add(scale3(Z2[4 * x + mu], 0.75), scale3(Z1[4 * x + mu], -8.0 / 9.0)),
+                             scale3(Z0[4 * x + mu], 17.0 / 36.0));
+                store_link(W, x, mu, mul(expm3(X), link_at(W, x, mu)));
+            }
+    }
+    memcpy(Uout, W, sizeof(double) * n);
+    memcpy(chiout, c, sizeof(double) * f * nrhs);
+    free(W);
+    free(c);
+    free(d0);
+    free(l1);
+    free(l2);
+    free(tmp);
+    free(Z0);
+    free(Z1);
+    free(Z2);
+}
+
 /* ------------------------------------------------------------------ */
 /* Quenched Hybrid Monte Carlo (Sec. 3.1, HMC! with leapfrog)           */
 /* ------------------------------------------------------------------ */

@@ -847,3 +847,82 @@ def test_hmc_trivial_cases_and_metropolis():
     if p < 1.0:
         acc_hi, _, U_hi = oracle.hmc(dims, U, beta, 0.2, 4, mom, 1.000001 * p)
         assert not acc_hi and np.array_equal(U_hi, U)
+
+
+# --------------------------------------------------------------------------
+# fermion gradient flow (covariant Laplacian, RK3 with the gauge stages)
+# --------------------------------------------------------------------------
+
+def _laplace_p(p):
+    """Eigenvalue of the free covariant Laplacian on a plane wave: -sum 4 sin^2(p/2)."""
+    return -sum(4 * np.sin(pm / 2) ** 2 for pm in p)
+
+
+@pytest.mark.parametrize("theta", [(1, 1, 1, -1), (np.exp(0.7j), np.exp(-1.1j), 1, np.exp(2.3j))])
+def test_laplacian_free_plane_waves_and_rk3_step_factor(theta):
+    dims = (4, 2, 6, 4)
+    U = inputs.unit_gauge_field(dims)
+    ps = _momenta(dims, theta)
+    x, y, z, t = _coords(dims)
+    rng = np.random.default_rng(7)
+    eps, n = 0.05, 4
+    for nn in [(0, 0, 0, 0), (1, 1, 2, 3), (3, 0, 5, 1)]:
+        p = [ps[mu][nn[mu]] for mu in range(4)]
+        phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+        u = rng.normal(size=(4, 3)) + 1j * rng.normal(size=(4, 3))
+        psi = phase[..., None, None] * u
+        lam = _laplace_p(p)
+        assert rel(oracle.laplacian(dims, U, psi, theta=theta), lam * psi) < 1e-13
+        # unit links stay unit under the Wilson flow, so each step multiplies the
+        # plane wave by the RK3 polynomial of h = eps lam
+        h = eps * lam
+        Uf, cf = oracle.fermion_flow(dims, U, psi, eps, n, theta=theta)
+        assert np.max(np.abs(Uf - U)) == 0.0
+        assert rel(cf, (1 + h + h * h / 2 + h ** 3 / 6) ** n * psi) < 1e-13
+
+
+def test_laplacian_is_hermitian_negative_and_covariant():
+    dims, U = _rough()
+    th = (np.exp(0.4j), 1, np.exp(-0.8j), -1)
+    a = inputs.spinor_field(dims, seed=21)
+    b = inputs.spinor_field(dims, seed=22)
+    la, lb = oracle.laplacian(dims, U, a, theta=th), oracle.laplacian(dims, U, b, theta=th)
+    assert abs(vdot(a, lb) - vdot(la, b)) <= 1e-14 * abs(vdot(a, lb))
+    assert vdot(a, la).real < 0 and abs(vdot(a, la).imag) <= 1e-13 * abs(vdot(a, la))
+    g = inputs.gauge_transform(dims, seed=23)
+    ga = np.einsum("...ab,...sb->...sa", g, a)
+    lhs = oracle.laplacian(dims, _transform(U, g), ga, theta=th)
+    assert rel(lhs, np.einsum("...ab,...sb->...sa", g, la)) < 1e-14
+    # colour only: the same operator on every spin component
+    a0 = a.copy()
+    a0[..., 1:, :] = 0
+    assert np.max(np.abs(oracle.laplacian(dims, U, a0, theta=th)[..., 1:, :])) == 0.0
+
+
+def test_fermion_flow_third_order_gauge_part_covariance_linearity():
+    dims = (4, 4, 2, 4)
+    U = inputs.gauge_field(dims, 0.3, seed=63)
+    chi = inputs.spinor_field(dims, seed=64, nrhs=2)
+    th = (1, np.exp(0.5j), 1, -1)
+    t = 0.24
+    _, ref = oracle.fermion_flow(dims, U, chi, t / 192, 192, theta=th, nrhs=2)
+    errs = [np.max(np.abs(oracle.fermion_flow(dims, U, chi, t / n, n, theta=th, nrhs=2)[1] - ref))
+            for n in (6, 12, 24)]
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 6.5 < e1 / e2 < 11.0, errs  # ~2^3 per halving: third order in the coupled system
+    Uf, cf = oracle.fermion_flow(dims, U, chi, 0.02, 5, theta=th, nrhs=2)
+    assert np.max(np.abs(Uf - oracle.wilson_flow(dims, U, 0.02, 5))) == 0.0  # no back-reaction
+    # each field flows on its own and linearly
+    _, c0 = oracle.fermion_flow(dims, U, chi[0], 0.02, 5, theta=th)
+    _, cs = oracle.fermion_flow(dims, U, 2.0 * chi[0] - 3.0j * chi[1], 0.02, 5, theta=th)
+    assert rel(cf[0], c0) < 1e-15
+    assert rel(cs, 2.0 * cf[0] - 3.0j * cf[1]) < 1e-13
+    # gauge covariance: flowing transformed fields gives the transformed flow
+    g = inputs.gauge_transform(dims, seed=65)
+    Ufg, cfg = oracle.fermion_flow(dims, _transform(U, g), np.einsum("...ab,...sb->...sa", g, chi), 0.02, 5,
+                                   theta=th, nrhs=2)
+    assert np.max(np.abs(Ufg - _transform(Uf, g))) < 1e-13
+    assert rel(cfg, np.einsum("...ab,...sb->...sa", g, cf)) < 1e-13
+    # the flow smooths: the norm decreases step by step
+    norms = [np.linalg.norm(oracle.fermion_flow(dims, U, chi, 0.02, k, theta=th, nrhs=2)[1]) for k in range(4)]
+    assert all(b < a for a, b in zip(norms, norms[1:]))
