@@ -74,6 +74,7 @@ def _load():
         lib.oracle_wilson_flow.argtypes = [ip, dp, ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_laplacian.argtypes = [ip, dp, dp, dp, dp]
         lib.oracle_fermion_flow.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, dp, dp]
+        lib.oracle_fermion_backflow.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, dp]
         lib.oracle_hmc.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, ctypes.c_double, dp,
                                    dp]
         lib.oracle_hmc.restype = ctypes.c_int
@@ -262,6 +263,17 @@ def fermion_flow(dims, U, chi, eps, nsteps, theta=DEFAULT_THETA, nrhs=1):
     _load().oracle_fermion_flow(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), _dp(th), float(eps),
                                 int(nsteps), _dp(chi), int(nrhs), _dp(Uo), _dp(co))
     return Uo, co
+
+
+def fermion_backflow(dims, U, eta, eps, nsteps, theta=DEFAULT_THETA, nrhs=1):
+    """Adjoint (back-)flow of nrhs quark fields from t = nsteps eps to 0 through the
+    Wilson flow that starts at U (the exact adjoint of fermion_flow's discrete steps)."""
+    U, eta, th, d = _c128(U), _c128(eta), _theta(theta), _dims(dims)
+    assert eta.size == nrhs * 12 * int(np.prod(dims))
+    out = np.zeros_like(eta)
+    _load().oracle_fermion_backflow(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), _dp(th), float(eps),
+                                    int(nsteps), _dp(eta), int(nrhs), _dp(out))
+    return out
 
 
 def hmc(dims, U, beta, eps, nsteps, mom, u):

@@ -994,6 +994,80 @@ void oracle_fermion_flow(const int *L, const double *U, const double *theta, dou
     free(Z2);
 }
 
+/* The gauge stages W1, W2 of one Wilson-flow step from W0 (those of
+ * oracle_wilson_flow). */
+static void flow_stage_fields(const int L[4], const double *W0, double eps, double *W1, double *W2)
+{
+    const long V = volume_of(L);
+    mat3 *Z0 = malloc(sizeof(mat3) * 4 * V), *Z1 = malloc(sizeof(mat3) * 4 * V);
+    memcpy(W1, W0, sizeof(double) * 72 * V);
+    for (long x = 0; x < V; ++x)
+        for (int mu = 0; mu < 4; ++mu) Z0[4 * x + mu] = scale3(flow_generator(L, W0, x, mu), eps);
+    for (long x = 0; x < V; ++x)
+        for (int mu = 0; mu < 4; ++mu)
+            store_link(W1, x, mu, mul(expm3(scale3(Z0[4 * x + mu], 0.25)), link_at(W0, x, mu)));
+    memcpy(W2, W1, sizeof(double) * 72 * V);
+    for (long x = 0; x < V; ++x)
+        for (int mu = 0; mu < 4; ++mu) Z1[4 * x + mu] = scale3(flow_generator(L, W1, x, mu), eps);
+    for (long x = 0; x < V; ++x)
+        for (int mu = 0; mu < 4; ++mu) {
+            mat3 X = add(scale3(Z1[4 * x + mu], 8.0 / 9.0), scale3(Z0[4 * x + mu], -17.0 / 36.0));
+            store_link(W2, x, mu, mul(expm3(X), link_at(W1, x, mu)));
+        }
+    free(Z0);
+    free(Z1);
+}
+
+/* Adjoint flow of quark fields (Sec. 3.2: the correlators of flowed fields
+ * need "the integration of the adjoint flow equations", backflowing the
+ * fermion field through stored gauge fields).  Reading: the exact adjoint of
+ * the discrete forward flow of oracle_fermion_flow.  One forward step is
+ *   chi' = M chi,  M = (1 + a D0) + d D2 + d b D2 D1 (1 + a D0) - d c D2 D0
+ * (a = eps/4, b = 8 eps/9, c = 2 eps/9, d = 3 eps/4; Di = Delta(Wi), each
+ * Hermitian), so one backward step is
+ *   eta <- M^dag eta = eta + z2 + z1 + D0 (a eta + a z1 - c z2),
+ *   z2 = d D2 eta,  z1 = b D1 z2,
+ * applied for the steps in reverse order.  Each step's gauge stages are
+ * rebuilt from the field at the step's start, itself obtained by flowing the
+ * start field forward (the plain form of the checkpointing the paper
+ * describes).  U: the gauge field at flow time 0 (not changed); eta: nrhs
+ * fields at t = nsteps eps; etaout (may alias eta): the fields at 0. */
+void oracle_fermion_backflow(const int *L, const double *U, const double *theta, double eps, int nsteps,
+                             const double *eta, int nrhs, double *etaout)
+{
+    const long V = volume_of(L), n = 72 * V, f = 24 * V;
+    const double a = 0.25 * eps, b = 8.0 / 9.0 * eps, c = 2.0 / 9.0 * eps, d = 0.75 * eps;
+    cplx th[4];
+    for (int mu = 0; mu < 4; ++mu) th[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
+    double *W0 = malloc(sizeof(double) * n), *W1 = malloc(sizeof(double) * n), *W2 = malloc(sizeof(double) * n);
+    double *e = malloc(sizeof(double) * f * nrhs), *z1 = malloc(sizeof(double) * f), *z2 = malloc(sizeof(double) * f);
+    double *w = malloc(sizeof(double) * f), *t0 = malloc(sizeof(double) * f);
+    memcpy(e, eta, sizeof(double) * f * nrhs);
+    for (int k = nsteps - 1; k >= 0; --k) {
+        oracle_wilson_flow(L, U, eps, k, W0);  /* the field at the start of step k */
+        flow_stage_fields(L, W0, eps, W1, W2);
+        for (int j = 0; j < nrhs; ++j) {
+            double *ej = e + f * j;
+            laplacian(L, W2, th, ej, t0);
+            axpby(f, d, t0, 0.0, t0, z2);          /* z2 = d D2 eta */
+            laplacian(L, W1, th, z2, t0);
+            axpby(f, b, t0, 0.0, t0, z1);          /* z1 = b D1 z2 */
+            for (long q = 0; q < f; ++q) w[q] = a * ej[q] + a * z1[q] - c * z2[q];
+            laplacian(L, W0, th, w, t0);           /* D0 (a eta + a z1 - c z2) */
+            for (long q = 0; q < f; ++q) ej[q] = ej[q] + z2[q] + z1[q] + t0[q];
+        }
+    }
+    memcpy(etaout, e, sizeof(double) * f * nrhs);
+    free(W0);
+    free(W1);
+    free(W2);
+    free(e);
+    free(z1);
+    free(z2);
+    free(w);
+    free(t0);
+}
+
 /* ------------------------------------------------------------------ */
 /* Quenched Hybrid Monte Carlo (Sec. 3.1, HMC! with leapfrog)           */
 /* ------------------------------------------------------------------ */

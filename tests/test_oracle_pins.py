@@ -926,3 +926,31 @@ def test_fermion_flow_third_order_gauge_part_covariance_linearity():
     # the flow smooths: the norm decreases step by step
     norms = [np.linalg.norm(oracle.fermion_flow(dims, U, chi, 0.02, k, theta=th, nrhs=2)[1]) for k in range(4)]
     assert all(b < a for a, b in zip(norms, norms[1:]))
+
+
+def test_fermion_backflow_is_the_adjoint_of_the_flow():
+    dims = (4, 4, 2, 4)
+    th = (1, np.exp(0.5j), np.exp(-0.2j), -1)
+    U = inputs.gauge_field(dims, 0.3, seed=66)
+    chi = inputs.spinor_field(dims, seed=67, nrhs=2)
+    eta = inputs.spinor_field(dims, seed=68, nrhs=2)
+    for eps, n in ((0.03, 4), (0.05, 2)):
+        _, fc = oracle.fermion_flow(dims, U, chi, eps, n, theta=th, nrhs=2)
+        be = oracle.fermion_backflow(dims, U, eta, eps, n, theta=th, nrhs=2)
+        for j in range(2):
+            lhs, rhs = vdot(eta[j], fc[j]), vdot(be[j], chi[j])
+            assert abs(lhs - rhs) <= 1e-14 * abs(lhs)
+    assert np.array_equal(oracle.fermion_backflow(dims, U, eta, 0.03, 0, theta=th, nrhs=2), eta)
+    # covariance, and the free plane wave takes the forward step factor (h is real)
+    g = inputs.gauge_transform(dims, seed=69)
+    be = oracle.fermion_backflow(dims, U, eta[0], 0.03, 3, theta=th)
+    bg = oracle.fermion_backflow(dims, _transform(U, g), np.einsum("...ab,...sb->...sa", g, eta[0]), 0.03, 3,
+                                 theta=th)
+    assert rel(bg, np.einsum("...ab,...sb->...sa", g, be)) < 1e-13
+    ps = _momenta(dims, th)
+    x, y, z, t = _coords(dims)
+    p = [ps[mu][(1, 2, 1, 3)[mu]] for mu in range(4)]
+    psi = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))[..., None, None] * np.ones((4, 3))
+    h = 0.05 * _laplace_p(p)
+    got = oracle.fermion_backflow(dims, inputs.unit_gauge_field(dims), psi, 0.05, 3, theta=th)
+    assert rel(got, (1 + h + h * h / 2 + h ** 3 / 6) ** 3 * psi) < 1e-13
