@@ -67,13 +67,13 @@ HOP_BYTES_PER_RHS = {"hop_f16_hopclov": 104.0, "hop_f16_selfclov": 156.0}
 HOP_BYTES_SHARED = {"hop_f16_hopclov": 336.0, "hop_f16_selfclov": 336.0}
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
 # one ncu capture (24^3x48, 331776 sites per parity, staged paired kernel;
-# its summary is kept under profiles/): 509.1 MB for hopclov and 722.3 MB
+# its summary is kept under profiles/): 509.0 MB for hopclov and 722.0 MB
 # for selfclov.  Every operand is read once per site, so the traffic scales
 # with the sites of a launch (the paired kernel the autotuner may pick for
 # hopclov moves the same bytes, 509.8 MB in the same capture setting).
 # Valid only for the kernel sources the capture was taken on (digest
 # below); otherwise the bench reports null.
-HOP_TRAFFIC = {"digest": "f85561fb0030f471", "hop_f16_hopclov": 509.10e6 / 331776, "hop_f16_selfclov": 722.35e6 / 331776}
+HOP_TRAFFIC = {"digest": "59e0902ca05600c9", "hop_f16_hopclov": 509.02e6 / 331776, "hop_f16_selfclov": 721.97e6 / 331776}
 KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh", "hopp_inst.cuh", "hops.cuh"]
 
 
@@ -572,10 +572,23 @@ def flow_measure(lqcd, dims=(32, 32, 32, 32), eps=0.01, steps=5):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         e1 = float(np.sum(lqcd.gauge_observables(lat, gid, dims[3])[1]))
+        # the fermion flow of 12 quark fields (a propagator's columns) alongside the links
+        chi = torch.randn(12 * inputs.volume(dims) * 24, dtype=torch.float64, device="cuda")
+        dp = lqcd.dirac_params(0.13, 0.0)
+        lqcd.fermion_flow(lat, gid, dp, chi, eps, 1, nrhs=12)  # warm-up
+        torch.cuda.synchronize()
+        a.record()
+        lqcd.fermion_flow(lat, gid, dp, chi, eps, 2, nrhs=12)
+        b.record()
+        torch.cuda.synchronize()
+        ms_f = a.elapsed_time(b) / 2
+        del chi
     finally:
         lqcd.lattice_destroy(lat)
+    torch.cuda.empty_cache()
     return {"lattice": list(dims), "eps": eps, "ms_per_step": ms, "t10_s_est": ms * 1000 / 1e3,
-            "E_plaq_sum_before_after": [e0, e1], "arithmetic": "FP64"}
+            "E_plaq_sum_before_after": [e0, e1], "fermion_flow_12_fields_ms_per_step": ms_f,
+            "arithmetic": "FP64"}
 
 
 # ---------------------------------------------------------------------------
@@ -589,7 +602,7 @@ SERVE = {"sizes": [[8, 8, 8, 16], [16, 16, 16, 32], [24, 24, 24, 48], [32, 32, 3
 def serving_pretune(lqcd):
     """Runs the hop autotuner for every served size before a request stream
     starts (one Dhat application per size and storage format the mixed solver
-    uses: FP16 inner, FP32 coarse updates, FP64 updates), as a server would at
+    uses: FP16 inner, FP32 incremental updates, FP64 updates), as a server would at
     start-up; otherwise the first request of a size tunes while the other
     slots' kernels share the GPU and its timings are contaminated.  Returns
     the tuner's decisions for the served sizes."""
@@ -928,7 +941,8 @@ def run_ours(args):
                                                                      "batched_vs_sequential_mixed",
                                                                      "batched_vs_sequential_fp64_est")},
             "meson_ms": None if not meson else meson["ms"],
-            "flow_32c4": None if not flow else {k: flow[k] for k in ("ms_per_step", "t10_s_est")},
+            "flow_32c4": None if not flow else {k: flow[k] for k in ("ms_per_step", "t10_s_est",
+                                                                     "fermion_flow_12_fields_ms_per_step")},
         }
         # the JSON line is kept short (rounded, summaries only); the full legs go to stderr
         print(json.dumps({"bench_details": {"kernels": per_kernel, "tuning": lqcd.tune_report(), "dslash": dslash,

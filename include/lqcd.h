@@ -313,6 +313,44 @@ int lqcd_boundary_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *
  * Errors: LQCD_EINVAL (unknown id, eps <= 0, nsteps < 0), LQCD_ENOMEM, LQCD_ECUDA. */
 int lqcd_gauge_flow(lqcd_lattice lat, int gauge_id, double eps, int nsteps, void *stream);
 
+/* Fermion gradient flow (Sec. 3.2: the flow of quark fields following
+ * Luescher's 2013 construction, which the paper cites): the resident links
+ * are flowed exactly as by lqcd_gauge_flow and the nrhs quark fields psi
+ * alongside, d psi/dt = Delta psi with the covariant Laplacian
+ *   (Delta psi)(x) = sum_mu [U~_mu(x) psi(x+mu) + U~_mu(x-mu)^dag psi(x-mu) - 2 psi(x)]
+ * (colour only; U~ carries the boundary phases theta of dp, the other fields
+ * of dp are not used), by the third-order scheme on the gauge stages W0, W1,
+ * W2 of each step:
+ *   lambda1 = psi + eps/4 Delta(W0) psi,
+ *   lambda2 = psi + 8 eps/9 Delta(W1) lambda1 - 2 eps/9 Delta(W0) psi,
+ *   psi(t + eps) = lambda1 + 3 eps/4 Delta(W2) lambda2;  FP64.
+ * psi: nrhs full-lattice fields in the host layout, overwritten with the
+ * flowed fields (host memory, or device memory with LQCD_DEVICE_PTRS).
+ * Errors: LQCD_EINVAL (unknown id, null pointer, eps <= 0, nsteps < 0,
+ * nrhs < 1, bc other than periodic), LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_fermion_flow(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, double *psi, int nrhs,
+                      double eps, int nsteps, int flags, void *stream);
+
+/* Fermion backflow (Sec. 3.2: correlators of flowed quark fields need "the
+ * integration of the adjoint flow equations", the fermion field backflowed
+ * through stored gauge fields): the exact adjoint of the steps of
+ * lqcd_fermion_flow, applied to eta from flow time t = nsteps eps back to 0
+ * through the Wilson flow that starts at the resident links.  With one
+ * forward step psi' = M psi, one backward step is eta <- M^dag eta =
+ *   u + z2 + Delta(W0) (eps/4 u - 2 eps/9 z2),  u = eta + z1,
+ *   z2 = 3 eps/4 Delta(W2) eta,  z1 = 8 eps/9 Delta(W1) z2,
+ * so <eta, F psi> = <B eta, psi> holds for the discrete flows F and B.  The
+ * gauge field at the start of every step is rebuilt from nsave >= 1
+ * checkpoints (one every ceil(nsteps / nsave) steps), each segment being
+ * flowed again from its checkpoint: device memory for nsave + ceil(nsteps /
+ * nsave) + 3 gauge fields and 5 nrhs-field quark fields.  The resident links
+ * are not changed.  eta: nrhs full-lattice fields in the host layout (host
+ * memory, or device memory with LQCD_DEVICE_PTRS), overwritten.
+ * Errors: LQCD_EINVAL (unknown id, null pointer, eps <= 0, nsteps < 0,
+ * nrhs < 1, nsave < 1, bc other than periodic), LQCD_ENOMEM, LQCD_ECUDA. */
+int lqcd_fermion_backflow(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, double *eta, int nrhs,
+                          double eps, int nsteps, int nsave, int flags, void *stream);
+
 /* Gauge observables of a resident field (plaquette, Eoft_plaq, Eoft_clover
  * and Qtop of Sec. 3.2), FP64, host outputs (any may be NULL):
  *   *plaq    = (1 / 6V) sum_x sum_{mu<nu} Re tr U_p(x) / 3   (1 for the unit field),

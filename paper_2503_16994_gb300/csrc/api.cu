@@ -169,6 +169,62 @@ int lqcd_gauge_flow(lqcd_lattice lat, int gauge_id, double eps, int nsteps, void
     API_CATCH
 }
 
+int lqcd_fermion_flow(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, double *psi, int nrhs,
+                      double eps, int nsteps, int flags, void *stream)
+{
+    if (!lat || !dp || !psi) return fail(LQCD_EINVAL, "null argument");
+    if (!(eps > 0.0) || !std::isfinite(eps) || nsteps < 0) return fail(LQCD_EINVAL, "eps must be > 0, nsteps >= 0");
+    if (nrhs < 1) return fail(LQCD_EINVAL, "nrhs must be >= 1");
+    if (int rc = check_params(dp)) return rc;
+    if (dp->bc != LQCD_BC_PERIODIC) return fail(LQCD_EINVAL, "the flow is built for periodic boundaries only");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(double) * 24 * (size_t)lat->V * nrhs;
+    double *d = psi;
+    if (!(flags & LQCD_DEVICE_PTRS)) {
+        lat->staging.ensure(bytes);
+        LQCD_CUDA(cudaMemcpyAsync(lat->staging.p, psi, bytes, cudaMemcpyHostToDevice, st));
+        d = lat->staging.as<double>();
+    }
+    fermion_flow(lat, *it->second, *dp, d, nrhs, eps, nsteps, st);
+    if (!(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(psi, d, bytes, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    return LQCD_OK;
+    API_CATCH
+}
+
+int lqcd_fermion_backflow(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *dp, double *eta, int nrhs,
+                          double eps, int nsteps, int nsave, int flags, void *stream)
+{
+    if (!lat || !dp || !eta) return fail(LQCD_EINVAL, "null argument");
+    if (!(eps > 0.0) || !std::isfinite(eps) || nsteps < 0) return fail(LQCD_EINVAL, "eps must be > 0, nsteps >= 0");
+    if (nrhs < 1 || nsave < 1) return fail(LQCD_EINVAL, "nrhs and nsave must be >= 1");
+    if (int rc = check_params(dp)) return rc;
+    if (dp->bc != LQCD_BC_PERIODIC) return fail(LQCD_EINVAL, "the flow is built for periodic boundaries only");
+    API_TRY
+    std::lock_guard<std::mutex> lk(lat->mu);
+    DeviceGuard dg(lat->device);
+    auto it = lat->gauges.find(gauge_id);
+    if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(double) * 24 * (size_t)lat->V * nrhs;
+    double *d = eta;
+    if (!(flags & LQCD_DEVICE_PTRS)) {
+        lat->staging.ensure(bytes);
+        LQCD_CUDA(cudaMemcpyAsync(lat->staging.p, eta, bytes, cudaMemcpyHostToDevice, st));
+        d = lat->staging.as<double>();
+    }
+    fermion_backflow(lat, *it->second, *dp, d, nrhs, eps, nsteps, nsave, st);
+    if (!(flags & LQCD_DEVICE_PTRS)) LQCD_CUDA(cudaMemcpyAsync(eta, d, bytes, cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA(cudaStreamSynchronize(st));
+    return LQCD_OK;
+    API_CATCH
+}
+
 int lqcd_gauge_observables(lqcd_lattice lat, int gauge_id, double *plaq, double *Eplaq, double *Eclov, double *Q,
                            void *stream)
 {

@@ -319,34 +319,205 @@ __global__ void __launch_bounds__(128) gauge_unpack_kernel(Geom g, long V, const
     }
 }
 
+// one stage of the low-storage RK3 step (W_stage -> W_stage+1) of the links
+// u (FP64 planes), X the stage accumulator
+static void flow_stage(lqcd_lattice_s *lat, double2 *u, double2 *X, int stage, double eps, cudaStream_t st)
+{
+    const long S = lat->stride;
+    const dim3 gf(unsigned((lat->vh + 63) / 64), 2, 4), gu(unsigned((lat->vh + 127) / 128), 2, 4);
+    // per link: 6 staples of 2 products and a product with the link (~13 3x3 complex products)
+    const double fbytes = double(lat->V) * 4 * (7 * 144.0 + 144.0), ubytes = double(lat->V) * 4 * 3 * 144.0;
+    const LinkField<F64> U{u, nullptr, S};
+    const double a[3] = {0.25, 8.0 / 9.0, 0.75}, b[3] = {0.0, -17.0 / 9.0, -1.0};
+    {
+        ProfScope prof("flow_force", fbytes, st);
+        flow_force_kernel<<<gf, 64, 0, st>>>(lat->geom, U, X, a[stage] * eps, b[stage]);
+        LQCD_CHECK_LAUNCH();
+    }
+    ProfScope prof("flow_update", ubytes, st);
+    flow_update_kernel<<<gu, 128, 0, st>>>(lat->geom, u, X, 1.0);
+    LQCD_CHECK_LAUNCH();
+}
+
+// the FP32/FP16 copies of the flowed links; the clover fields of the old links are dropped
+static void flow_finish(lqcd_lattice_s *lat, GaugeSet &g, cudaStream_t st)
+{
+    const dim3 gr(unsigned((lat->vh + 127) / 128), 8);
+    recon_copies_kernel<<<gr, 128, 0, st>>>(lat->geom, g.u64.as<const double2>(), g.u32.as<float4>(),
+                                            g.u16.as<uint4>(), g.u16b.as<uint2>());
+    LQCD_CHECK_LAUNCH();
+    LQCD_CUDA(cudaStreamSynchronize(st));  // scratch buffers are freed on return
+    g.clover.clear();
+}
+
 void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaStream_t st)
 {
     const long S = lat->stride;
     DevBuf X;
     X.ensure(sizeof(double2) * 2 * 4 * 9 * S);
-    const dim3 gf(unsigned((lat->vh + 63) / 64), 2, 4), gu(unsigned((lat->vh + 127) / 128), 2, 4);
-    // per link: 6 staples of 2 products and a product with the link (~13 3x3 complex products)
-    const double fbytes = double(lat->V) * 4 * (7 * 144.0 + 144.0), ubytes = double(lat->V) * 4 * 3 * 144.0;
-    double2 *u = g.u64.as<double2>();
-    const LinkField<F64> U{u, nullptr, S};
-    const double a[3] = {0.25, 8.0 / 9.0, 0.75}, b[3] = {0.0, -17.0 / 9.0, -1.0};
     for (int k = 0; k < nsteps; ++k)
-        for (int stage = 0; stage < 3; ++stage) {
-            {
-                ProfScope prof("flow_force", fbytes, st);
-                flow_force_kernel<<<gf, 64, 0, st>>>(lat->geom, U, X.as<double2>(), a[stage] * eps, b[stage]);
-                LQCD_CHECK_LAUNCH();
-            }
-            ProfScope prof("flow_update", ubytes, st);
-            flow_update_kernel<<<gu, 128, 0, st>>>(lat->geom, u, X.as<const double2>(), 1.0);
-            LQCD_CHECK_LAUNCH();
+        for (int stage = 0; stage < 3; ++stage) flow_stage(lat, g.u64.as<double2>(), X.as<double2>(), stage, eps, st);
+    flow_finish(lat, g, st);
+}
+
+// ---------------------------------------------------------------------------
+// Fermion flow: d chi/dt = Delta chi with the covariant Laplacian
+//   (Delta chi)(x) = sum_mu [U~_mu(x) chi(x+mu) + U~_mu(x-mu)^dag chi(x-mu) - 2 chi(x)]
+// (colour only; U~ carries the boundary phases theta), the links flowed
+// alongside.  Third-order scheme on the gauge stages W0, W1, W2 of a step:
+//   lambda1 = chi + eps/4 Delta(W0) chi
+//   lambda2 = chi + 8 eps/9 Delta(W1) lambda1 - 2 eps/9 Delta(W0) chi
+//   chi'    = lambda1 + 3 eps/4 Delta(W2) lambda2
+// With Delta(W0) chi = 4 (lambda1 - chi) / eps and H the hopping sum this is
+//   lambda1 = eps/4 H chi + (1 - 2 eps) chi
+//   lambda2 = 8 eps/9 H lambda1 - 8/9 (1 + 8 eps) lambda1 + 17/9 chi
+//   chi'    = 3 eps/4 H lambda2 - 6 eps lambda2 + lambda1
+// so each stage is one pass per parity of
+//   out(x) = cH H in (x) + c0 in(x) + c1 a1(x).
+// ---------------------------------------------------------------------------
+struct Phases {
+    double re[4], im[4];
+};
+
+__global__ void __launch_bounds__(128) laplace_kernel(Geom g, int p, LinkField<F64> U, Phases th,
+                                                      SpinorField<F64> self, SpinorField<F64> other,
+                                                      SpinorField<F64> a1, SpinorField<F64> a2, SpinorField<F64> out,
+                                                      int nrhs, double cH, double c0, double c1, double c2)
+{
+    const int j = blockIdx.x % nrhs, tile = blockIdx.x / nrhs;
+    const int cb = tile * blockDim.x + threadIdx.x;
+    if (cb >= g.vh) return;
+    int x[4];
+    cb_coords(g, p, cb, x);
+    spinor<double> acc;
+    zero(acc);
+    for (int mu = 0; mu < 4; ++mu) {
+        int y[4];
+        shift(g, x, mu, +1, y);
+        int ycb = cb_index(g, y);
+        const su3<double> Uf = load_link<F64, double>(U, p, mu, cb);
+        spinor<double> v = load_spinor<F64, double>(other, j, ycb);
+        cx<double> ph = x[mu] == g.L[mu] - 1 ? cx<double>{th.re[mu], th.im[mu]} : cx<double>{1.0, 0.0};
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc.s[s][a] = acc.s[s][a] + ph * (Uf.m[a][0] * v.s[s][0] + Uf.m[a][1] * v.s[s][1] + Uf.m[a][2] * v.s[s][2]);
+        shift(g, x, mu, -1, y);
+        ycb = cb_index(g, y);
+        const su3<double> Ub = load_link<F64, double>(U, p ^ 1, mu, ycb);
+        v = load_spinor<F64, double>(other, j, ycb);
+        ph = x[mu] == 0 ? cx<double>{th.re[mu], -th.im[mu]} : cx<double>{1.0, 0.0};
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc.s[s][a] = acc.s[s][a] + ph * (cmul(Ub.m[0][a], v.s[s][0]) + cmul(Ub.m[1][a], v.s[s][1]) +
+                                                   cmul(Ub.m[2][a], v.s[s][2]));
+    }
+    const spinor<double> sv = load_spinor<F64, double>(self, j, cb);
+    spinor<double> res;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) res.s[s][a] = cH * acc.s[s][a] + c0 * sv.s[s][a];
+    if (a1.p) {
+        const spinor<double> av = load_spinor<F64, double>(a1, j, cb);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) res.s[s][a] = res.s[s][a] + c1 * av.s[s][a];
+    }
+    if (a2.p) {
+        const spinor<double> av = load_spinor<F64, double>(a2, j, cb);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) res.s[s][a] = res.s[s][a] + c2 * av.s[s][a];
+    }
+    store_spinor<F64, double>(out, j, cb, res);
+}
+
+// backflow combination: u = eta + z1; w = a u - c z2 (one parity, every RHS)
+__global__ void __launch_bounds__(128) backflow_combine_kernel(long vh, int nrhs, SpinorField<F64> eta,
+                                                               SpinorField<F64> z1, SpinorField<F64> z2,
+                                                               SpinorField<F64> u, SpinorField<F64> w, double a,
+                                                               double c)
+{
+    const int j = blockIdx.x % nrhs, tile = blockIdx.x / nrhs;
+    const int cb = tile * blockDim.x + threadIdx.x;
+    if (cb >= vh) return;
+    const spinor<double> e = load_spinor<F64, double>(eta, j, cb), p1 = load_spinor<F64, double>(z1, j, cb),
+                         p2 = load_spinor<F64, double>(z2, j, cb);
+    spinor<double> uu, ww;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uu.s[s][k] = e.s[s][k] + p1.s[s][k];
+            ww.s[s][k] = a * uu.s[s][k] - c * p2.s[s][k];
         }
-    const dim3 gr(unsigned((lat->vh + 127) / 128), 8);
-    recon_copies_kernel<<<gr, 128, 0, st>>>(lat->geom, g.u64.as<const double2>(), g.u32.as<float4>(),
-                                            g.u16.as<uint4>(), g.u16b.as<uint2>());
-    LQCD_CHECK_LAUNCH();
-    LQCD_CUDA(cudaStreamSynchronize(st));  // X is freed on return
-    g.clover.clear();                      // the clover fields belong to the old links
+    store_spinor<F64, double>(u, j, cb, uu);
+    store_spinor<F64, double>(w, j, cb, ww);
+}
+
+namespace {
+// a full-lattice FP64 field: even and odd halves of nrhs right-hand sides
+struct Full {
+    SpinorField<F64> e, o;
+    const SpinorField<F64> &half(int p) const { return p ? o : e; }
+};
+
+Full full_of(DevBuf &b, long stride, int nrhs)
+{
+    double2 *p = b.as<double2>();
+    const long half = (long)12 * stride * nrhs;
+    return Full{SpinorField<F64>{p, nullptr, stride}, SpinorField<F64>{p + half, nullptr, stride}};
+}
+}  // namespace
+
+// out = cH H in + c0 in + c1 a1 + c2 a2 on both parities (in != out; a1, a2 may be null)
+static void laplace_stage(lqcd_lattice_s *lat, const LinkField<F64> &U, const Phases &th, const Full &in,
+                          const Full *a1, const Full &out, int nrhs, double cH, double c0, double c1, cudaStream_t st,
+                          const Full *a2 = nullptr, double c2 = 0.0)
+{
+    // per output site and RHS: the spinor at 8 neighbours and itself (+ a1, a2), the output; 8 links per site
+    const double bytes = double(lat->vh) * (nrhs * 192.0 * (2.0 + (a1 ? 1.0 : 0.0) + (a2 ? 1.0 : 0.0)) + 8 * 144.0);
+    for (int p = 0; p < 2; ++p) {
+        ProfScope prof("fermion_flow_laplace", bytes, st);
+        laplace_kernel<<<unsigned(ntiles_of(lat->vh) * nrhs), kBlock, 0, st>>>(
+            lat->geom, p, U, th, in.half(p), in.half(p ^ 1), a1 ? a1->half(p) : SpinorField<F64>{},
+            a2 ? a2->half(p) : SpinorField<F64>{}, out.half(p), nrhs, cH, c0, c1, c2);
+        LQCD_CHECK_LAUNCH();
+    }
+}
+
+void fermion_flow(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, double *psi_dev, int nrhs,
+                  double eps, int nsteps, cudaStream_t st)
+{
+    const long S = lat->stride;
+    const size_t fb = sizeof(double2) * 2 * 12 * (size_t)S * nrhs;
+    DevBuf X, bchi, bl1, bl2;
+    X.ensure(sizeof(double2) * 2 * 4 * 9 * S);
+    bchi.ensure(fb);
+    bl1.ensure(fb);
+    bl2.ensure(fb);
+    const Full chi = full_of(bchi, S, nrhs), l1 = full_of(bl1, S, nrhs), l2 = full_of(bl2, S, nrhs);
+    Phases th;
+    hop_theta(dp, th.re, th.im);
+    const LinkField<F64> U{g.u64.as<const double2>(), nullptr, S};
+    spinor_to_soa(lat, psi_dev, nrhs, chi.e, chi.o, st);
+    for (int k = 0; k < nsteps; ++k) {
+        laplace_stage(lat, U, th, chi, nullptr, l1, nrhs, 0.25 * eps, 1.0 - 2.0 * eps, 0.0, st);  // W0
+        flow_stage(lat, g.u64.as<double2>(), X.as<double2>(), 0, eps, st);
+        laplace_stage(lat, U, th, l1, &chi, l2, nrhs, 8.0 / 9.0 * eps, -8.0 / 9.0 * (1.0 + 8.0 * eps), 17.0 / 9.0,
+                      st);  // W1
+        flow_stage(lat, g.u64.as<double2>(), X.as<double2>(), 1, eps, st);
+        laplace_stage(lat, U, th, l2, &l1, chi, nrhs, 0.75 * eps, -6.0 * eps, 1.0, st);  // W2
+        flow_stage(lat, g.u64.as<double2>(), X.as<double2>(), 2, eps, st);
+    }
+    spinor_from_soa(lat, psi_dev, nrhs, chi.e, chi.o, st);
+    flow_finish(lat, g, st);
 }
 
 // S = (beta / 6) sum_t Eplaq[t] from the observables kernel (host value)
@@ -443,6 +614,87 @@ void gauge_download(lqcd_lattice_s *lat, GaugeSet &g, double *U_dev, cudaStream_
     gauge_unpack_kernel<<<unsigned((lat->V + 127) / 128), 128, 0, st>>>(lat->geom, lat->V, g.u64.as<const double2>(),
                                                                         U_dev);
     LQCD_CHECK_LAUNCH();
+}
+
+}  // namespace lqcd
+
+namespace lqcd {
+
+// ---------------------------------------------------------------------------
+// Fermion backflow: the exact adjoint of the forward steps above, run over the
+// steps in reverse order.  One forward step is chi' = M chi with
+//   M = (1 + a D0) + d D2 + d b D2 D1 (1 + a D0) - d c D2 D0,
+// a = eps/4, b = 8 eps/9, c = 2 eps/9, d = 3 eps/4, Di = Delta(Wi) (Hermitian),
+// so one backward step is
+//   z2 = d D2 eta,  z1 = b D1 z2,  u = eta + z1,  w = a u - c z2,
+//   eta <- u + z2 + D0 w.
+// The gauge field at the start of every step is rebuilt from checkpoints:
+// a forward pass keeps the field at the start of every m-th step (m =
+// ceil(nsteps / nsave)); each segment of m steps is then flowed again from
+// its checkpoint, keeping the start field of each of its steps, and walked
+// backwards; the stages W1, W2 of a step are recomputed from its start field.
+// The resident links are left at flow time 0.
+// ---------------------------------------------------------------------------
+void fermion_backflow(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, double *eta_dev, int nrhs,
+                      double eps, int nsteps, int nsave, cudaStream_t st)
+{
+    const long S = lat->stride;
+    const size_t ub = sizeof(double2) * 2 * 4 * 9 * (size_t)S;  // one gauge field
+    const size_t fb = sizeof(double2) * 2 * 12 * (size_t)S * nrhs;
+    const int m = nsteps > 0 ? (nsteps + nsave - 1) / nsave : 1;
+    const int nck = nsteps > 0 ? (nsteps + m - 1) / m : 0;
+    DevBuf X, ck, seg, w1, w2, be, bz1, bz2, bu, bw;
+    X.ensure(ub);
+    ck.ensure(ub * std::max(nck, 1));
+    seg.ensure(ub * m);
+    w1.ensure(ub);
+    w2.ensure(ub);
+    for (DevBuf *b : {&be, &bz1, &bz2, &bu, &bw}) b->ensure(fb);
+    const Full eta = full_of(be, S, nrhs), z1 = full_of(bz1, S, nrhs), z2 = full_of(bz2, S, nrhs),
+               u = full_of(bu, S, nrhs), w = full_of(bw, S, nrhs);
+    const size_t nlink = ub / sizeof(double2);
+    double2 *ckp = ck.as<double2>(), *segp = seg.as<double2>(), *W1 = w1.as<double2>(), *W2 = w2.as<double2>();
+    Phases th;
+    hop_theta(dp, th.re, th.im);
+    spinor_to_soa(lat, eta_dev, nrhs, eta.e, eta.o, st);
+    // forward pass: checkpoints at the start of steps 0, m, 2m, ... (w1 is the running field)
+    LQCD_CUDA(cudaMemcpyAsync(W1, g.u64.p, ub, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < nsteps; ++k) {
+        if (k % m == 0) LQCD_CUDA(cudaMemcpyAsync(ckp + (k / m) * nlink, W1, ub, cudaMemcpyDeviceToDevice, st));
+        if (k + 1 < nsteps)  // the end field of the last step is not needed
+            for (int stage = 0; stage < 3; ++stage) flow_stage(lat, W1, X.as<double2>(), stage, eps, st);
+    }
+    const double a = 0.25 * eps, b = 8.0 / 9.0 * eps, c = 2.0 / 9.0 * eps, d = 0.75 * eps;
+    const unsigned gvec = unsigned(ntiles_of(lat->vh) * nrhs);
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+        const int k0 = sgi * m, k1 = std::min(nsteps, k0 + m);
+        // start fields of the steps k0 .. k1-1 of this segment
+        LQCD_CUDA(cudaMemcpyAsync(segp, ckp + sgi * nlink, ub, cudaMemcpyDeviceToDevice, st));
+        for (int k = k0 + 1; k < k1; ++k) {
+            double2 *dst = segp + (k - k0) * nlink;
+            LQCD_CUDA(cudaMemcpyAsync(dst, dst - nlink, ub, cudaMemcpyDeviceToDevice, st));
+            for (int stage = 0; stage < 3; ++stage) flow_stage(lat, dst, X.as<double2>(), stage, eps, st);
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            double2 *W0 = segp + (k - k0) * nlink;
+            LQCD_CUDA(cudaMemcpyAsync(W1, W0, ub, cudaMemcpyDeviceToDevice, st));
+            flow_stage(lat, W1, X.as<double2>(), 0, eps, st);
+            LQCD_CUDA(cudaMemcpyAsync(W2, W1, ub, cudaMemcpyDeviceToDevice, st));
+            flow_stage(lat, W2, X.as<double2>(), 1, eps, st);
+            const LinkField<F64> U0{W0, nullptr, S}, U1{W1, nullptr, S}, U2{W2, nullptr, S};
+            laplace_stage(lat, U2, th, eta, nullptr, z2, nrhs, d, -8.0 * d, 0.0, st);  // z2 = d D2 eta
+            laplace_stage(lat, U1, th, z2, nullptr, z1, nrhs, b, -8.0 * b, 0.0, st);   // z1 = b D1 z2
+            for (int p = 0; p < 2; ++p) {
+                ProfScope prof("fermion_backflow_combine", double(lat->vh) * nrhs * 5 * 192.0, st);
+                backflow_combine_kernel<<<gvec, kBlock, 0, st>>>(lat->vh, nrhs, eta.half(p), z1.half(p), z2.half(p),
+                                                                 u.half(p), w.half(p), a, c);
+                LQCD_CHECK_LAUNCH();
+            }
+            laplace_stage(lat, U0, th, w, &u, eta, nrhs, 1.0, -8.0, 1.0, st, &z2, 1.0);  // eta = u + z2 + D0 w
+        }
+    }
+    spinor_from_soa(lat, eta_dev, nrhs, eta.e, eta.o, st);
+    LQCD_CUDA(cudaStreamSynchronize(st));  // scratch buffers are freed on return
 }
 
 }  // namespace lqcd

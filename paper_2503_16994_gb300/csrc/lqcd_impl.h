@@ -196,6 +196,15 @@ void hop_theta(const lqcd_dirac_params &dp, double th_re[4], double th_im[4]);
 // (plaquette / 3, plaquette and clover action densities, clover charge
 // density), and the links in the host layout (gauge_flow.cu)
 void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaStream_t st);
+// the same flow with nrhs quark fields (host layout, on the device) flowed
+// alongside by the covariant Laplacian (theta of dp), in place
+void fermion_flow(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, double *psi_dev, int nrhs,
+                  double eps, int nsteps, cudaStream_t st);
+// the exact adjoint of fermion_flow's steps, run backwards from t = nsteps eps
+// to 0 through the flow that starts at the resident links (left unchanged);
+// nsave gauge-field checkpoints
+void fermion_backflow(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, double *eta_dev, int nrhs,
+                      double eps, int nsteps, int nsave, cudaStream_t st);
 void gauge_observables(lqcd_lattice_s *lat, GaugeSet &g, double *out_dev, cudaStream_t st);
 void gauge_download(lqcd_lattice_s *lat, GaugeSet &g, double *U_dev, cudaStream_t st);
 // one leapfrog HMC trajectory of the resident links with the caller's momenta

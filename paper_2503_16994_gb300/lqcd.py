@@ -100,6 +100,10 @@ def load():
         "lqcd_pion_corr_batch": [ctypes.POINTER(PionJob), ctypes.c_int, ctypes.POINTER(SolverParams), ctypes.c_int, vp],
         "lqcd_pion_contract_noalloc": [ip, vp, ctypes.c_int, vp, vp],
         "lqcd_gauge_flow": [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp],
+        "lqcd_fermion_flow": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), vp, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_int, ctypes.c_int, vp],
+        "lqcd_fermion_backflow": [vp, ctypes.c_int, ctypes.POINTER(DiracParams), vp, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
         "lqcd_gauge_observables": [vp, ctypes.c_int, dp, dp, dp, dp, vp],
         "lqcd_gauge_download": [vp, ctypes.c_int, vp, ctypes.c_int, vp],
         "lqcd_hmc_trajectory": [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp,
@@ -325,6 +329,39 @@ def pion_corr(lat, gauge_id, params: DiracParams, solver: SolverParams, src, dim
 def gauge_flow(lat, gauge_id, eps, nsteps, stream=None):
     """Wilson flow (RK3) of the resident field, in place: t = nsteps * eps."""
     _check(load().lqcd_gauge_flow(lat, int(gauge_id), float(eps), int(nsteps), stream))
+
+
+def fermion_flow(lat, gauge_id, params: DiracParams, psi, eps, nsteps, nrhs=1, stream=None):
+    """Flows the resident links (as gauge_flow) and nrhs quark fields alongside
+    (lqcd_fermion_flow).  A CUDA tensor is flowed in place and returned; a
+    host array is copied, and the flowed copy is returned."""
+    if _is_cuda_tensor(psi):
+        n = psi.numel() * (2 if psi.is_complex() else 1)
+        _check(load().lqcd_fermion_flow(lat, int(gauge_id), ctypes.byref(params), _dev_ptr(psi, n), int(nrhs),
+                                        float(eps), int(nsteps), DEVICE_PTRS, _stream_of(psi, stream)))
+        return psi
+    p = np.array(_host(psi), copy=True)
+    if p.size != nrhs * 12 * int(np.prod(p.shape[-6:-2])):
+        raise ValueError("psi must hold nrhs full-lattice quark fields")
+    _check(load().lqcd_fermion_flow(lat, int(gauge_id), ctypes.byref(params), p.ctypes.data_as(ctypes.c_void_p),
+                                    int(nrhs), float(eps), int(nsteps), 0, None))
+    return p
+
+
+def fermion_backflow(lat, gauge_id, params: DiracParams, eta, eps, nsteps, nrhs=1, nsave=4, stream=None):
+    """Adjoint flow of nrhs quark fields from t = nsteps eps to 0 (lqcd_fermion_backflow); the
+    resident links stay at t = 0.  A CUDA tensor is changed in place; a host array is copied."""
+    if _is_cuda_tensor(eta):
+        n = eta.numel() * (2 if eta.is_complex() else 1)
+        _check(load().lqcd_fermion_backflow(lat, int(gauge_id), ctypes.byref(params), _dev_ptr(eta, n), int(nrhs),
+                                            float(eps), int(nsteps), int(nsave), DEVICE_PTRS, _stream_of(eta, stream)))
+        return eta
+    p = np.array(_host(eta), copy=True)
+    if p.size != nrhs * 12 * int(np.prod(p.shape[-6:-2])):
+        raise ValueError("eta must hold nrhs full-lattice quark fields")
+    _check(load().lqcd_fermion_backflow(lat, int(gauge_id), ctypes.byref(params), p.ctypes.data_as(ctypes.c_void_p),
+                                        int(nrhs), float(eps), int(nsteps), int(nsave), 0, None))
+    return p
 
 
 def gauge_observables(lat, gauge_id, T):
