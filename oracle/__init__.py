@@ -70,6 +70,14 @@ def _load():
         lib.oracle_boundary_corr.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                              ctypes.c_double, ctypes.c_int, dp, dp, dp, ip, dp]
         lib.oracle_boundary_corr.restype = ctypes.c_int
+        lib.oracle_dirac_sf.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                        ctypes.c_int]
+        lib.oracle_cgnr_sf.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                       ctypes.c_double, ctypes.c_int, ip, dp]
+        lib.oracle_cgnr_sf.restype = ctypes.c_int
+        lib.oracle_boundary_corr_sf.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                                                ctypes.c_double, ctypes.c_int, dp, dp, dp, ip, dp]
+        lib.oracle_boundary_corr_sf.restype = ctypes.c_int
         lib.oracle_gauge_obs.argtypes = [ip, dp, dp, dp, dp, dp]
         lib.oracle_wilson_flow.argtypes = [ip, dp, ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_laplacian.argtypes = [ip, dp, dp, dp, dp]
@@ -222,6 +230,43 @@ def boundary_corr(dims, U, kappa, csw, cF, theta=DEFAULT_THETA, tol=1e-13, maxit
                                           _dp(th), tol, maxiter, _dp(fP), _dp(fA),
                                           _dp(H) if H is not None else None,
                                           iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(res))
+    return fP, fA, H, iters, res, failed
+
+
+def dirac_sf(dims, U, kappa, csw, cF, psi, theta=DEFAULT_THETA, dagger=False) -> np.ndarray:
+    """D (or D^dag) with Schroedinger-functional boundaries (slice 0 the boundary) and coefficient cF."""
+    U, psi, th, d = _c128(U), _c128(psi), _theta(theta), _dims(dims)
+    out = np.zeros_like(psi)
+    _load().oracle_dirac_sf(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, cF, _dp(th),
+                            _dp(psi), _dp(out), int(bool(dagger)))
+    return out
+
+
+def cgnr_sf(dims, U, kappa, csw, cF, b, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000):
+    """Solves the SF D x = b by CGNR; returns (x, iterations, true relative residual, converged)."""
+    U, b, th, d = _c128(U), _c128(b), _theta(theta), _dims(dims)
+    x = np.zeros_like(b)
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0)
+    st = _load().oracle_cgnr_sf(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw, cF, _dp(th),
+                                _dp(b), _dp(x), tol, maxiter, ctypes.byref(it), ctypes.byref(res))
+    return x, it.value, res.value, st == 0
+
+
+def boundary_corr_sf(dims, U, kappa, csw, cF, theta=DEFAULT_THETA, tol=1e-13, maxiter=100000, want_prop=False):
+    """SF f_P(x_t), f_A(x_t) from the six sources U_t(0)^dag P+ e_j on slice 1.
+
+    Returns (fP, fA, H or None [6, T, Z, Y, X, 4, 3], iterations[6], residuals[6], failed_columns)."""
+    lx, ly, lz, lt = dims
+    U, th, d = _c128(U), _theta(theta), _dims(dims)
+    fP, fA = np.zeros(lt), np.zeros(lt)
+    H = np.zeros((6, lt, lz, ly, lx, 4, 3), dtype=np.complex128) if want_prop else None
+    iters = np.zeros(6, dtype=np.int32)
+    res = np.zeros(6)
+    failed = _load().oracle_boundary_corr_sf(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(U), kappa, csw,
+                                             cF, _dp(th), tol, maxiter, _dp(fP), _dp(fA),
+                                             _dp(H) if H is not None else None,
+                                             iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(res))
     return fP, fA, H, iters, res, failed
 
 

@@ -294,6 +294,7 @@ typedef struct {
     cplx theta[4];
     double *F; /* clover field F[site][plane][3][3], NULL when csw == 0 */
     int open;   /* open boundary in time: the links U_t(x) with x_t = T - 1 are absent */
+    int sf;     /* Schroedinger-functional boundary: slice x_t = 0 is the boundary (identity there) */
     double cF;  /* boundary improvement coefficient on the slices x_t = 0 and T - 1 (open only) */
     double *Uopen; /* the gauge field with the absent links set to zero (owned; open only) */
 } dirac_ctx;
@@ -310,6 +311,7 @@ static void ctx_init(dirac_ctx *c, const int *L, const double *U, double kappa, 
     for (int mu = 0; mu < 4; ++mu) c->theta[mu] = theta[2 * mu] + I * theta[2 * mu + 1];
     c->F = NULL;
     c->open = 0;
+    c->sf = 0;
     c->cF = 1.0;
     c->Uopen = NULL;
     if (csw != 0.0) {
@@ -337,6 +339,42 @@ static void ctx_init_open(dirac_ctx *c, const int *L, const double *U, double ka
     c->cF = cF;
 }
 
+/* Schroedinger-functional boundary conditions (Sec. 2.1, BC_SF_ORBI and
+ * BC_SF_AFWB; the two differ only in the boundary weights of improved gauge
+ * actions, so for the quark fields of the Wilson-clover operator they read
+ * the same).  Read as the standard SF with homogeneous quark boundary values:
+ * the time extent T runs from the boundary x_t = 0 to the boundary x_t = T,
+ * which is stored as the slice x_t = 0 again (so both boundaries carry the
+ * field's links of slice 0); the quark field lives on the slices 1 .. T - 1
+ * and vanishes on the boundaries.  So every hop that reaches the slice 0 is
+ * absent, the operator is the identity on the slice 0 (which then decouples:
+ * a source that vanishes there gives a solution that vanishes there), the
+ * clover term on 1 .. T - 1 is built from all links (the boundary ones
+ * included), and the slices 1 and T - 1 get the boundary improvement term
+ * 2 kappa (cF - 1) (cF = c~_t of DiracParam, Sec. 3.3).  theta_t plays no part. */
+static void ctx_init_sf(dirac_ctx *c, const int *L, const double *U, double kappa, double csw,
+                        const double *theta, double cF)
+{
+    long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2];
+    ctx_init(c, L, U, kappa, csw, theta); /* the clover field from every link */
+    double *Uz = malloc(sizeof(double) * 72 * V);
+    memcpy(Uz, U, sizeof(double) * 72 * V);
+    for (long s = 0; s < V3; ++s) memset(Uz + 18 * 4 * s, 0, sizeof(double) * 72);   /* links at x_t = 0 */
+    for (long s = (long)(L[3] - 1) * V3; s < V; ++s) memset(Uz + 18 * (4 * s + 3), 0, sizeof(double) * 18);
+    c->U = Uz; /* the hops */
+    c->Uopen = Uz;
+    c->sf = 1;
+    c->cF = cF;
+}
+
+/* slices that carry the boundary improvement term */
+static int improved_slice(const dirac_ctx *c, int t)
+{
+    if (c->open) return t == 0 || t == c->L[3] - 1;
+    if (c->sf) return t == 1 || t == c->L[3] - 1;
+    return 0;
+}
+
 static void ctx_free(dirac_ctx *c)
 {
     free(c->F);
@@ -361,6 +399,7 @@ static spinor dirac_site(const dirac_ctx *c, const double *psi, long x)
     int xc[4];
     coords_of(L, x, xc);
     spinor out = spinor_at(psi, x);
+    if (c->sf && xc[3] == 0) return out; /* the SF boundary slice */
     for (int mu = 0; mu < 4; ++mu) {
         /* forward: -kappa (1 - g_mu) U~_mu(x) psi(x+mu) */
         long y = step(L, x, mu, +1);
@@ -393,7 +432,7 @@ static spinor dirac_site(const dirac_ctx *c, const double *psi, long x)
         for (int al = 0; al < 4; ++al)
             for (int a = 0; a < 3; ++a) out.c[al][a] += 2.0 * I * c->kappa * c->mu * G[4][al][al] * s.c[al][a];
     }
-    if (c->open && (xc[3] == 0 || xc[3] == L[3] - 1)) {
+    if (improved_slice(c, xc[3])) {
         /* boundary improvement: + 2 kappa (cF - 1) psi(x) on the first and last slice */
         spinor s = spinor_at(psi, x);
         for (int al = 0; al < 4; ++al)
@@ -426,6 +465,7 @@ static void dirac_dagger_apply(const dirac_ctx *c, const double *in, double *out
         /* diagonal: 1 + clover^dag */
         for (int al = 0; al < 4; ++al)
             for (int a = 0; a < 3; ++a) acc[x].c[al][a] += px.c[al][a];
+        if (c->sf && xc[3] == 0) continue; /* the SF boundary slice: identity, no hops */
         if (c->F) {
             for (int p = 0; p < 6; ++p) {
                 int mu = PLANE[p][0], nu = PLANE[p][1];
@@ -445,7 +485,7 @@ static void dirac_dagger_apply(const dirac_ctx *c, const double *in, double *out
                 for (int a = 0; a < 3; ++a)
                     acc[x].c[al][a] += -2.0 * I * c->kappa * c->mu * G[4][al][al] * px.c[al][a];
         }
-        if (c->open && (xc[3] == 0 || xc[3] == L[3] - 1)) {
+        if (improved_slice(c, xc[3])) {
             /* the boundary term is real and diagonal: its own adjoint */
             for (int al = 0; al < 4; ++al)
                 for (int a = 0; a < 3; ++a) acc[x].c[al][a] += 2.0 * c->kappa * (c->cF - 1.0) * px.c[al][a];
@@ -688,30 +728,36 @@ int oracle_cgnr_open(const int *L, const double *U, double kappa, double csw, do
  * (P+ e_{j+6} = -P+ e_j, so the six columns are all there is.)  H (may be
  * NULL) receives the columns [6][site][12] complex; iters, resid (may be
  * NULL) per column.  Returns the number of columns that did not converge. */
-int oracle_boundary_corr(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
-                         double tol, int maxiter, double *fP, double *fA, double *H, int *iters, double *resid)
+/* The boundary-to-bulk correlators on the operator of c; sf: the sources sit
+ * on the slice 1, W_j(1, yvec) = U_t(0, yvec)^dag P+ e_j (the hop from the SF
+ * boundary field), else on the slice 0, W_j(0, yvec) = P+ e_j. */
+static int boundary_corr_ctx(dirac_ctx *c, const int *L, const double *U, int sf, double tol, int maxiter,
+                             double *fP, double *fA, double *H, int *iters, double *resid)
 {
-    init_gamma();
     const long V = volume_of(L), V3 = (long)L[0] * L[1] * L[2], n = 24 * V;
     double *S = H ? H : malloc(sizeof(double) * 6 * n);
     double *w = calloc((size_t)n, sizeof(double));
-    dirac_ctx c;
-    ctx_init_open(&c, L, U, kappa, csw, theta, cF);
     int failed = 0;
     for (int j = 0; j < 6; ++j) {
         memset(w, 0, sizeof(double) * n);
-        for (long y = 0; y < V3; ++y)       /* the slice y_t = 0 */
-            for (int al = 0; al < 4; ++al) { /* (P+ e_j)_al = (delta_{al,s} + (g_t)_{al,s}) / 2 */
-                const int s = j / 3, col = j % 3;
+        const int s = j / 3, col = j % 3;
+        for (long y = 0; y < V3; ++y) {
+            const long site = sf ? y + V3 : y; /* the slice 1 or 0 */
+            mat3 u = dag(link_at(U, y, 3));    /* U_t(0, yvec)^dag (sf only) */
+            for (int al = 0; al < 4; ++al) {  /* (P+ e_j)_al = (delta_{al,s} + (g_t)_{al,s}) / 2 */
                 cplx v = 0.5 * ((al == s ? 1.0 : 0.0) + G[3][al][s]);
-                w[24 * y + 2 * (3 * al + col)] = creal(v);
-                w[24 * y + 2 * (3 * al + col) + 1] = cimag(v);
+                for (int a = 0; a < 3; ++a) {
+                    cplx va = sf ? v * u.m[a][col] : (a == col ? v : 0.0);
+                    w[24 * site + 2 * (3 * al + a)] = creal(va);
+                    w[24 * site + 2 * (3 * al + a) + 1] = cimag(va);
+                }
             }
+        }
         double *x = S + (long)j * n;
         memset(x, 0, sizeof(double) * n);
         int it;
         double res;
-        failed += cgnr_ctx(&c, L, w, x, tol, maxiter, &it, &res);
+        failed += cgnr_ctx(c, L, w, x, tol, maxiter, &it, &res);
         if (iters) iters[j] = it;
         if (resid) resid[j] = res;
     }
@@ -728,9 +774,59 @@ int oracle_boundary_corr(const int *L, const double *U, double kappa, double csw
                     fA[t] -= creal(conj(h.c[al][a]) * gh);
                 }
         }
-    ctx_free(&c);
     free(w);
     if (!H) free(S);
+    return failed;
+}
+
+int oracle_boundary_corr(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                         double tol, int maxiter, double *fP, double *fA, double *H, int *iters, double *resid)
+{
+    init_gamma();
+    dirac_ctx c;
+    ctx_init_open(&c, L, U, kappa, csw, theta, cF);
+    int failed = boundary_corr_ctx(&c, L, U, 0, tol, maxiter, fP, fA, H, iters, resid);
+    ctx_free(&c);
+    return failed;
+}
+
+void oracle_dirac_sf(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                     const double *in, double *out, int dagger)
+{
+    dirac_ctx c;
+    ctx_init_sf(&c, L, U, kappa, csw, theta, cF);
+    if (dagger)
+        dirac_dagger_apply(&c, in, out);
+    else
+        dirac_apply(&c, in, out);
+    ctx_free(&c);
+}
+
+/* CGNR of oracle_cgnr on the SF operator */
+int oracle_cgnr_sf(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                   const double *b, double *x, double tol, int maxiter, int *iters, double *resid)
+{
+    dirac_ctx c;
+    ctx_init_sf(&c, L, U, kappa, csw, theta, cF);
+    int st = cgnr_ctx(&c, L, b, x, tol, maxiter, iters, resid);
+    ctx_free(&c);
+    return st;
+}
+
+/* f_P, f_A with SF boundaries (Sec. 3.3: the boundary-to-bulk propagators of
+ * the Dirichlet boundaries give f_P and f_A for SF boundary conditions):
+ * H_j = D_SF^-1 W_j with the six sources W_j(1, yvec) = U_t(0, yvec)^dag P+ e_j
+ * on every site of the first dynamical slice (the boundary quark field
+ * P+ e_j at x_t = 0 carried in by the time link; zero spatial momentum), and
+ * fP, fA per slice as for the open boundary (no 1/2, no 1/L^3). */
+int oracle_boundary_corr_sf(const int *L, const double *U, double kappa, double csw, double cF, const double *theta,
+                            double tol, int maxiter, double *fP, double *fA, double *H, int *iters, double *resid)
+{
+    init_gamma();
+    dirac_ctx c;
+    ctx_init_sf(&c, L, U, kappa, csw, theta, cF);
+    int failed = boundary_corr_ctx(&c, L, U, 1, tol, maxiter, fP, fA, H, iters, resid);
+    ctx_free(&c);
     return failed;
 }
 

@@ -954,3 +954,116 @@ def test_fermion_backflow_is_the_adjoint_of_the_flow():
     h = 0.05 * _laplace_p(p)
     got = oracle.fermion_backflow(dims, inputs.unit_gauge_field(dims), psi, 0.05, 3, theta=th)
     assert rel(got, (1 + h + h * h / 2 + h ** 3 / 6) ** 3 * psi) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Schroedinger-functional boundaries (slice 0 the boundary)
+# --------------------------------------------------------------------------
+
+def _sf_time_matrix(T, kappa, cF, p):
+    """(4T x 4T) matrix of the free SF operator on e^{i p.x} f(x_t) spinors: the
+    identity on x_t = 0; on 1 .. T-1 the site term of _time_matrix, 2 kappa (cF - 1)
+    added on x_t = 1 and T - 1, time hops only between the slices 1 .. T-1."""
+    M = _time_matrix(T, kappa, 1.0, p)
+    I4 = np.eye(4)
+    for t in (1, T - 1):
+        M[4 * t:4 * t + 4, 4 * t:4 * t + 4] += 2 * kappa * (cF - 1) * I4
+    M[0:4, :] = 0
+    M[:, 0:4] = 0
+    M[0:4, 0:4] = I4
+    return M
+
+
+def test_sf_free_field_plane_waves_in_space():
+    dims = (4, 6, 2, 7)
+    kappa, cF = 0.13, 1.37
+    theta = (np.exp(0.4j), np.exp(-1.1j), 1.0, np.exp(0.9j))  # theta_t plays no part
+    U = inputs.unit_gauge_field(dims)
+    rng = np.random.default_rng(6)
+    x, y, z = np.meshgrid(np.arange(dims[0]), np.arange(dims[1]), np.arange(dims[2]), indexing="ij")
+    for n in [(0, 0, 0), (1, 2, 1), (3, 5, 0)]:
+        p = [(np.angle(theta[k]) + 2 * np.pi * n[k]) / dims[k] for k in range(3)]
+        f = rng.normal(size=(dims[3], 4)) + 1j * rng.normal(size=(dims[3], 4))
+        wave = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z)).transpose(2, 1, 0)
+        col = rng.normal(size=3) + 1j * rng.normal(size=3)
+        psi = np.einsum("zyx,ts,c->tzyxsc", wave, f, col)
+        Mf = (_sf_time_matrix(dims[3], kappa, cF, p) @ f.reshape(-1)).reshape(dims[3], 4)
+        want = np.einsum("zyx,ts,c->tzyxsc", wave, Mf, col)
+        for csw in (0.0, 1.9):
+            got = oracle.dirac_sf(dims, U, kappa, csw, cF, psi, theta=theta)
+            assert rel(got, want) < 1e-14
+
+
+def test_sf_boundary_to_bulk_free_field():
+    """At unit links the sources U_t(0)^dag P+ e_j on slice 1 have zero spatial
+    momentum: H_j(x) = h_j(x_t) with M h_j = delta_{t,1} P+ e_j."""
+    dims = (4, 4, 2, 6)
+    kappa, cF = 0.12, 0.8
+    T, L3 = dims[3], dims[0] * dims[1] * dims[2]
+    fP, fA, H, iters, res, failed = oracle.boundary_corr_sf(dims, inputs.unit_gauge_field(dims), kappa, 1.0, cF,
+                                                            tol=1e-13)
+    assert failed == 0
+    M = _sf_time_matrix(T, kappa, cF, (0.0, 0.0, 0.0))
+    Pp = 0.5 * (np.eye(4) + BASIS[3])
+    wantP, wantA = np.zeros(T), np.zeros(T)
+    for s in range(2):
+        src = np.zeros(4 * T, complex)
+        src[4:8] = Pp[:, s]
+        h = np.linalg.solve(M, src).reshape(T, 4)
+        for t in range(T):
+            wantP[t] += 3 * L3 * np.vdot(h[t], h[t]).real
+            wantA[t] -= 3 * L3 * np.vdot(h[t], BASIS[3] @ h[t]).real
+    assert fP[0] == 0.0 and fA[0] == 0.0
+    assert np.allclose(fP, wantP, rtol=1e-11, atol=0)
+    assert np.allclose(fA, wantA, rtol=1e-10, atol=1e-12 * np.max(np.abs(wantP)))
+
+
+def test_sf_operator_identities_on_rough_fields():
+    """Rough field with clover: slice 0 is the identity and decouples; on 1 .. T-1
+    the SF operator is the periodic operator applied to the field with its slice
+    0 zeroed, plus 2 kappa (cF - 1) on the slices 1 and T-1, and the clover term
+    there is the periodic one (built from every link); gamma5-hermiticity, the
+    adjoint identity and gauge covariance hold."""
+    dims = (4, 4, 2, 6)
+    kappa, csw, cF = 0.125, 1.6, 1.3
+    T = dims[3]
+    U = inputs.gauge_field(dims, 0.5, seed=46)
+    a = inputs.spinor_field(dims, seed=47)
+    b = inputs.spinor_field(dims, seed=48)
+    th = (np.exp(0.3j), 1, 1, np.exp(1.2j))
+    D = lambda v, dag=False, UU=U: oracle.dirac_sf(dims, UU, kappa, csw, cF, v, theta=th, dagger=dag)
+    Da = D(a)
+    assert np.array_equal(Da[0], a[0])
+    a0 = a.copy()
+    a0[0] = 0
+    per = oracle.dirac(dims, U, kappa, csw, a0, theta=th)
+    bmask = np.zeros(dims[::-1])[..., None, None]
+    bmask[1] = bmask[T - 1] = 1.0
+    want = per + 2 * kappa * (cF - 1) * bmask * a0
+    assert rel(Da[1:], want[1:]) < 1e-14
+    assert rel(D(a0)[1:], Da[1:]) < 1e-15  # nothing on 1 .. T-1 reads the slice 0
+    assert abs(vdot(a, D(b)) - vdot(g5(D(g5(a))), b)) <= 1e-14 * abs(vdot(a, D(b)))
+    assert abs(vdot(a, D(b)) - vdot(D(a, True), b)) <= 1e-14 * abs(vdot(a, D(b)))
+    g = inputs.gauge_transform(dims, seed=49)
+    Ug = _transform(U, g)
+    assert rel(D(np.einsum("...ab,...sb->...sa", g, a), UU=Ug), np.einsum("...ab,...sb->...sa", g, D(a))) < 1e-14
+
+
+def test_sf_cgnr_matches_dense_inverse_and_vanishes_on_the_boundary():
+    dims = (2, 2, 2, 4)
+    kappa, csw, cF = 0.13, 1.4, 1.2
+    U = inputs.gauge_field(dims, 0.4, seed=50)
+    V = int(np.prod(dims))
+    n = 12 * V
+    M = np.zeros((n, n), complex)
+    for k in range(n):
+        e = np.zeros(n, complex)
+        e[k] = 1
+        M[:, k] = oracle.dirac_sf(dims, U, kappa, csw, cF, e.reshape(dims[::-1] + (4, 3))).reshape(-1)
+    b = inputs.spinor_field(dims, seed=51)
+    b[0] = 0  # the boundary carries no source
+    x, it, res, ok = oracle.cgnr_sf(dims, U, kappa, csw, cF, b, tol=1e-13)
+    assert ok
+    xd = np.linalg.solve(M, b.reshape(-1)).reshape(x.shape)
+    assert rel(x, xd) < 1e-11
+    assert np.max(np.abs(x[0])) < 1e-14 * np.max(np.abs(x))
