@@ -81,9 +81,15 @@ enum {
 /* boundary conditions in time (SpaceParm's BC of Sec. 2.1) */
 enum {
     LQCD_BC_PERIODIC = 0, /* every direction closes on itself, the hops across carry theta_mu */
-    LQCD_BC_OPEN = 1      /* open in time: no link from the slice x_t = T - 1 to x_t = 0 (hops and clover
+    LQCD_BC_OPEN = 1,     /* open in time: no link from the slice x_t = T - 1 to x_t = 0 (hops and clover
                              leaves across vanish, theta_t plays no part); the slices x_t = 0 and T - 1 get
                              the boundary improvement term 2 kappa (cF - 1) */
+    LQCD_BC_SF = 2        /* Schroedinger functional (BC_SF_ORBI / BC_SF_AFWB, which read the same for the
+                             quark fields), homogeneous quark boundary values: the slice x_t = 0 is the
+                             boundary at x_t = 0 and at x_t = T (its links, set by the caller to the
+                             boundary field, serve both); the operator is the identity there and no hop
+                             reaches it; the clover term on 1 .. T-1 uses every link; the slices 1 and
+                             T - 1 get 2 kappa (cF - 1); theta_t plays no part; mu must be 0 */
 };
 
 typedef struct lqcd_lattice_s *lqcd_lattice; /* opaque; owns all device memory it allocates */
@@ -99,8 +105,9 @@ typedef struct lqcd_server_s *lqcd_server;   /* opaque serving loop */
  * 2 kappa mu, is inverted as B_s - i s tau C_s with C_s = (A_s^2 + tau^2)^-1
  * and B_s = A_s C_s.  Solves at mu != 0 run on the generic (untuned) hopping
  * kernel in every storage format.  mu must be finite (LQCD_EINVAL).
- * bc: LQCD_BC_PERIODIC (0) or LQCD_BC_OPEN; cF: the boundary improvement
- * coefficient of DiracParam (Sec. 3.3), used with LQCD_BC_OPEN only (the T
+ * bc: LQCD_BC_PERIODIC (0), LQCD_BC_OPEN or LQCD_BC_SF; cF: the boundary
+ * improvement coefficient of DiracParam (Sec. 3.3, c~_t), used with LQCD_BC_OPEN
+ * and LQCD_BC_SF only (for LQCD_BC_OPEN the T
  * slices of the lattice are all dynamical; the paper's iL[4] - 1 effective
  * slices are this T).  A zero-initialised struct is the periodic operator. */
 typedef struct {
@@ -285,11 +292,13 @@ int lqcd_meson_contract(lqcd_lattice lat, const double *prop, int src_t, const d
                         int flags, void *stream);
 
 /* Boundary-to-bulk correlators (Sec. 3.3: the propagators from the boundary
- * that give f_P and f_A), on the operator of dp (meant for LQCD_BC_OPEN):
- * the six sources W_j(y) = delta_{y_t, 0} P+ e_j, j = 3 s + c with spin s in
- * {0, 1} and colour c, P+ = (1 + g_t) / 2, on every site of the slice y_t = 0
- * (zero spatial momentum; P+ e_{j+6} = -P+ e_j adds nothing), are solved as
- * one batch, H_j = D^-1 W_j, and per slice
+ * that give f_P and f_A), on the operator of dp (meant for LQCD_BC_OPEN or
+ * LQCD_BC_SF): the six sources W_j, j = 3 s + c with spin s in {0, 1} and
+ * colour c, P+ = (1 + g_t) / 2, zero spatial momentum (P+ e_{j+6} = -P+ e_j
+ * adds nothing) -- W_j(y) = delta_{y_t, 0} P+ e_j on every site of the slice
+ * y_t = 0 (open, periodic), or W_j(y) = delta_{y_t, 1} U_t(0, yvec)^dag P+ e_j
+ * on the slice 1 (SF: the boundary quark field carried in by the time link)
+ * -- are solved as one batch, H_j = D^-1 W_j, and per slice
  *   fP[x_t] = sum_xvec sum_j |H_j(x)|^2,
  *   fA[x_t] = - sum_xvec sum_j Re <H_j(x), g_t H_j(x)>.
  * fP, fA: T doubles each; H: NULL or 6 * 24 V doubles receiving the columns;
@@ -492,7 +501,8 @@ int lqcd_serve_gauge(lqcd_server srv, const int dims[4], const double *U, int *g
 
 /* Queues one 12-column point-source propagator + pion correlator request.
  * Copies its arguments; non-blocking.  *ticket identifies the request.
- * Errors: LQCD_EINVAL (unknown gauge id, bad source or params). */
+ * Errors: LQCD_EINVAL (unknown gauge id, bad source or params, bc other than
+ * LQCD_BC_PERIODIC or LQCD_BC_OPEN). */
 int lqcd_serve_submit(lqcd_server srv, int gauge_id, const lqcd_dirac_params *dp,
                       const lqcd_solver_params *sp, const int src[4], uint64_t *ticket);
 

@@ -41,8 +41,10 @@ static int check_params(const lqcd_dirac_params *dp)
     if (!(dp->kappa >= 0.0) || !std::isfinite(dp->kappa)) return fail(LQCD_EINVAL, "kappa must be finite and >= 0");
     if (!std::isfinite(dp->csw)) return fail(LQCD_EINVAL, "csw must be finite");
     if (!std::isfinite(dp->mu)) return fail(LQCD_EINVAL, "mu must be finite");
-    if (dp->bc != LQCD_BC_PERIODIC && dp->bc != LQCD_BC_OPEN) return fail(LQCD_EINVAL, "unknown boundary condition");
-    if (dp->bc == LQCD_BC_OPEN && !std::isfinite(dp->cF)) return fail(LQCD_EINVAL, "cF must be finite");
+    if (dp->bc != LQCD_BC_PERIODIC && dp->bc != LQCD_BC_OPEN && dp->bc != LQCD_BC_SF)
+        return fail(LQCD_EINVAL, "unknown boundary condition");
+    if (dp->bc != LQCD_BC_PERIODIC && !std::isfinite(dp->cF)) return fail(LQCD_EINVAL, "cF must be finite");
+    if (dp->bc == LQCD_BC_SF && dp->mu != 0.0) return fail(LQCD_EINVAL, "SF boundaries are built for mu = 0");
     for (int m = 0; m < 4; ++m)
         if (!std::isfinite(dp->theta_re[m]) || !std::isfinite(dp->theta_im[m]))
             return fail(LQCD_EINVAL, "theta must be finite");
@@ -444,7 +446,13 @@ int lqcd_boundary_corr(lqcd_lattice lat, int gauge_id, const lqcd_dirac_params *
     DevBuf fbuf;  // fP then fA on the device
     fbuf.ensure(sizeof(double) * 2 * T);
     double *f_d = fbuf.as<double>();
-    wall_sources_p_plus(lat, lat->staging.as<double>(), st);
+    if (dp->bc == LQCD_BC_SF) {
+        auto it = lat->gauges.find(gauge_id);
+        if (it == lat->gauges.end()) return fail(LQCD_EINVAL, "unknown gauge id");
+        wall_sources_sf(lat, *it->second, lat->staging.as<double>(), st);
+    } else {
+        wall_sources_p_plus(lat, lat->staging.as<double>(), st);
+    }
     int failed = solve(lat, gauge_id, *dp, *sp, lat->staging.as<const double>(), H_d, nullptr, 6, info, nullptr, st);
     const long nchunk = (lat->V / T + kBlock - 1) / kBlock;
     lat->red_partial.ensure(sizeof(double) * 2 * (size_t)T * nchunk);

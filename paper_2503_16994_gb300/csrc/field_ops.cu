@@ -25,6 +25,24 @@ LinkField<F16> link_field<F16>(const GaugeSet &g, long stride)
     return {g.u16.as<const uint4>(), g.u16b.as<const uint2>(), stride};
 }
 template <>
+LinkField<F64> hop_links<F64>(const GaugeSet &g, long stride, int bc)
+{
+    if (bc == LQCD_BC_SF) return {g.u64sf.as<const double2>(), nullptr, stride};
+    return link_field<F64>(g, stride);
+}
+template <>
+LinkField<F32> hop_links<F32>(const GaugeSet &g, long stride, int bc)
+{
+    if (bc == LQCD_BC_SF) return {g.u32sf.as<const float4>(), nullptr, stride};
+    return link_field<F32>(g, stride);
+}
+template <>
+LinkField<F16> hop_links<F16>(const GaugeSet &g, long stride, int bc)
+{
+    if (bc == LQCD_BC_SF) return {g.u16sf.as<const uint4>(), g.u16bsf.as<const uint2>(), stride};
+    return link_field<F16>(g, stride);
+}
+template <>
 CloverField<F64> clover_field<F64>(const CloverSet &c, bool inv, long stride)
 {
     return {(inv ? c.ainv64 : c.a64).as<const double2>(), stride};
@@ -96,8 +114,48 @@ __global__ void gauge_repack_kernel(Geom g, long V, const double *U, double2 *u6
     }
 }
 
+// Schroedinger-functional hopping links: every copy with the links U_mu(x) of
+// the boundary slice x_t = 0 and U_t(x) of x_t = T - 1 (which ends on the
+// boundary x_t = T, stored as slice 0) set to zero, so no hop reaches the
+// boundary slice in either direction
+__global__ void sf_links_kernel(Geom g, const double2 *u64, const float4 *u32, const uint4 *u16, const uint2 *u16b,
+                                double2 *s64, float4 *s32, uint4 *s16, uint2 *s16b)
+{
+    const long cb = long(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y, mu = blockIdx.z;
+    if (cb >= g.vh) return;
+    int x[4];
+    cb_coords(g, p, int(cb), x);
+    const bool zero = x[3] == 0 || (mu == 3 && x[3] == g.L[3] - 1);
+    const long q = p * 4 + mu;
+    for (int k = 0; k < 9; ++k)
+        s64[(q * 9 + k) * g.stride + cb] = zero ? make_double2(0.0, 0.0) : u64[(q * 9 + k) * g.stride + cb];
+    for (int k = 0; k < 3; ++k)
+        s32[(q * 3 + k) * g.stride + cb] = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : u32[(q * 3 + k) * g.stride + cb];
+    s16[q * g.stride + cb] = zero ? make_uint4(0u, 0u, 0u, 0u) : u16[q * g.stride + cb];
+    s16b[q * g.stride + cb] = zero ? make_uint2(0u, 0u) : u16b[q * g.stride + cb];
+}
+
+static void sf_links(lqcd_lattice_s *lat, GaugeSet &g, cudaStream_t st)
+{
+    if (g.sf_ready) return;
+    const long S = lat->stride;
+    g.u64sf.ensure(sizeof(double2) * 2 * 4 * 9 * S);
+    g.u32sf.ensure(sizeof(float4) * 2 * 4 * 3 * S);
+    g.u16sf.ensure(sizeof(uint4) * 2 * 4 * S);
+    g.u16bsf.ensure(sizeof(uint2) * 2 * 4 * S);
+    ProfScope prof("sf_links", double(lat->V) * 4 * 2 * (144.0 + 48.0 + 24.0), st);
+    sf_links_kernel<<<dim3(unsigned((lat->vh + kBlock - 1) / kBlock), 2, 4), kBlock, 0, st>>>(
+        lat->geom, g.u64.as<const double2>(), g.u32.as<const float4>(), g.u16.as<const uint4>(),
+        g.u16b.as<const uint2>(), g.u64sf.as<double2>(), g.u32sf.as<float4>(), g.u16sf.as<uint4>(),
+        g.u16bsf.as<uint2>());
+    LQCD_CHECK_LAUNCH();
+    g.sf_ready = true;
+}
+
 void gauge_repack(lqcd_lattice_s *lat, GaugeSet &g, const double *U_dev, cudaStream_t st)
 {
+    g.sf_ready = false;
     const long S = lat->stride;
     g.u64.ensure(sizeof(double2) * 2 * 4 * 9 * S);
     g.u32.ensure(sizeof(float4) * 2 * 4 * 3 * S);
@@ -170,9 +228,11 @@ __device__ void store_block(double2 *base, long stride, long cb, int off, const 
 // A_+- = 1 - i kc sum_k s_k (x) (B_k +- E_k), B = (F_yz, F_zx, F_xy), E_k = F_kt:
 // in 2x2 spin blocks of 3x3 colour matrices with M_k = B_k +- E_k,
 //   A = [[1 - i kc M_z, -i kc (M_x - i M_y)], [-i kc (M_x + i M_y), 1 + i kc M_z]].
-// open: open time boundary (absent links across it); cfterm: 2 kappa (cF - 1),
-// added to the site term on the first and last time slice when open
-__global__ void __launch_bounds__(64) clover_build_kernel(Geom g, LinkField<F64> U, double kc, double tau, bool open,
+// bc: LQCD_BC_OPEN: open time boundary (absent links across it), cfterm =
+// 2 kappa (cF - 1) added to the site term on the first and last time slice;
+// LQCD_BC_SF: Schroedinger-functional boundary at x_t = 0 (identity site term
+// there; clover leaves from every link), cfterm on the slices 1 and T - 1
+__global__ void __launch_bounds__(64) clover_build_kernel(Geom g, LinkField<F64> U, double kc, double tau, int bc,
                                                           double cfterm, double2 *a64, double2 *ainv64,
                                                           double2 *cinv64)
 {
@@ -181,10 +241,13 @@ __global__ void __launch_bounds__(64) clover_build_kernel(Geom g, LinkField<F64>
     if (cb >= g.vh) return;
     int x[4];
     cb_coords(g, p, cb, x);
+    const bool open = bc == LQCD_BC_OPEN, sf = bc == LQCD_BC_SF;
     m3 Fxy = field_strength(g, U, x, 0, 1, open), Fxz = field_strength(g, U, x, 0, 2, open);
     m3 Fxt = field_strength(g, U, x, 0, 3, open), Fyz = field_strength(g, U, x, 1, 2, open);
     m3 Fyt = field_strength(g, U, x, 1, 3, open), Fzt = field_strength(g, U, x, 2, 3, open);
-    const double diag = (open && (x[3] == 0 || x[3] == g.L[3] - 1)) ? 1.0 + cfterm : 1.0;
+    const bool improved = open ? (x[3] == 0 || x[3] == g.L[3] - 1) : (sf && (x[3] == 1 || x[3] == g.L[3] - 1));
+    const double diag = improved ? 1.0 + cfterm : 1.0;
+    if (sf && x[3] == 0) kc = 0.0;  // the boundary slice: identity site term
     for (int blk = 0; blk < 2; ++blk) {
         const double sg = blk == 0 ? 1.0 : -1.0;
         cd A[6][6], Ai[6][6];
@@ -263,7 +326,7 @@ std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, const 
                                         cudaStream_t st, bool async)
 {
     const double kc = dp.kappa * dp.csw;
-    const bool open = dp.bc == LQCD_BC_OPEN;
+    const bool bnd = dp.bc == LQCD_BC_OPEN || dp.bc == LQCD_BC_SF;
     auto c = std::make_unique<CloverSet>();
     c->tau = 2.0 * dp.kappa * dp.mu;
     const bool tw = c->tau != 0.0;
@@ -285,8 +348,8 @@ std::unique_ptr<CloverSet> clover_build(lqcd_lattice_s *lat, GaugeSet &g, const 
     }
     dim3 grid(unsigned((lat->vh + 63) / 64), 2);
     ProfScope prof("clover_build", double(lat->V) * (4 * 144.0 + (tw ? 3 : 2) * 576.0), st);
-    clover_build_kernel<<<grid, 64, 0, st>>>(lat->geom, link_field<F64>(g, S), kc, c->tau, open,
-                                             open ? 2.0 * dp.kappa * (dp.cF - 1.0) : 0.0, c->a64.as<double2>(),
+    clover_build_kernel<<<grid, 64, 0, st>>>(lat->geom, link_field<F64>(g, S), kc, c->tau, dp.bc,
+                                             bnd ? 2.0 * dp.kappa * (dp.cF - 1.0) : 0.0, c->a64.as<double2>(),
                                              c->ainv64.as<double2>(), tw ? c->cinv64.as<double2>() : nullptr);
     LQCD_CHECK_LAUNCH();
     dim3 g2(unsigned((lat->vh + kBlock - 1) / kBlock), 2);
@@ -312,9 +375,10 @@ void hop_theta(const lqcd_dirac_params &dp, double th_re[4], double th_im[4])
 
 CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, cudaStream_t st)
 {
-    const bool open = dp.bc == LQCD_BC_OPEN;
-    const auto key = std::make_tuple(dp.kappa * dp.csw, dp.kappa * dp.mu, int(open),
-                                     open ? dp.kappa * (dp.cF - 1.0) : 0.0);
+    if (dp.bc == LQCD_BC_SF) sf_links(lat, g, st);
+    const bool bnd = dp.bc == LQCD_BC_OPEN || dp.bc == LQCD_BC_SF;
+    const auto key = std::make_tuple(dp.kappa * dp.csw, dp.kappa * dp.mu, int(dp.bc),
+                                     bnd ? dp.kappa * (dp.cF - 1.0) : 0.0);
     auto it = g.clover.find(key);
     if (it != g.clover.end()) return *it->second;
     auto c = clover_build(lat, g, dp, st, false);
@@ -474,6 +538,42 @@ void wall_sources_p_plus(lqcd_lattice_s *lat, double *aos, cudaStream_t st)
     const long n = 6 * lat->V;
     ProfScope prof("wall_source", double(n) * 192.0, st);
     wall_source_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(lat->V, lat->V / lat->dims[3], aos);
+    LQCD_CHECK_LAUNCH();
+}
+
+// SF boundary sources W_j(1, yvec) = U_t(0, yvec)^dag P+ e_j on the slice 1
+// (host layout, 6 columns): component (alpha, a) = P+[alpha][s] conj(U_t(0, yvec)[c][a])
+__global__ void wall_source_sf_kernel(Geom g, long V, long v3, LinkField<F64> U, double *aos)
+{
+    const long i = long(blockIdx.x) * blockDim.x + threadIdx.x;  // (j, site) over 6 V
+    if (i >= 6 * V) return;
+    const int j = int(i / V);
+    const long x = i - long(j) * V;
+    double *o = aos + i * 24;
+    for (int k = 0; k < 24; ++k) o[k] = 0.0;
+    if (x >= v3 && x < 2 * v3) {
+        const long y = x - v3;  // the site below on the boundary slice
+        int xc[4];
+        lex_coords(g, y, xc);
+        const int p = (xc[0] + xc[1] + xc[2] + xc[3]) & 1;
+        const long cb = y >> 1;
+        const int s = j / 3, c = j % 3;
+        for (int a = 0; a < 3; ++a) {
+            const double2 u = U.p[((long)(p * 4 + 3) * 9 + 3 * c + a) * U.stride + cb];
+            o[2 * (3 * s + a)] = 0.5 * u.x;
+            o[2 * (3 * s + a) + 1] = -0.5 * u.y;
+            o[2 * (3 * (s + 2) + a)] = -0.5 * u.x;
+            o[2 * (3 * (s + 2) + a) + 1] = 0.5 * u.y;
+        }
+    }
+}
+
+void wall_sources_sf(lqcd_lattice_s *lat, const GaugeSet &g, double *aos, cudaStream_t st)
+{
+    const long n = 6 * lat->V;
+    ProfScope prof("wall_source", double(n) * 192.0, st);
+    wall_source_sf_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(lat->geom, lat->V, lat->V / lat->dims[3],
+                                                                     link_field<F64>(g, lat->stride), aos);
     LQCD_CHECK_LAUNCH();
 }
 

@@ -348,6 +348,7 @@ static void flow_finish(lqcd_lattice_s *lat, GaugeSet &g, cudaStream_t st)
     LQCD_CHECK_LAUNCH();
     LQCD_CUDA(cudaStreamSynchronize(st));  // scratch buffers are freed on return
     g.clover.clear();
+    g.sf_ready = false;  // the SF hopping links belong to the old links
 }
 
 void gauge_flow(lqcd_lattice_s *lat, GaugeSet &g, double eps, int nsteps, cudaStream_t st)
@@ -589,6 +590,7 @@ int hmc_trajectory(lqcd_lattice_s *lat, GaugeSet &g, double beta, double eps, in
     LQCD_CHECK_LAUNCH();
     LQCD_CUDA(cudaStreamSynchronize(st));
     g.clover.clear();
+    g.sf_ready = false;  // the SF hopping links belong to the old links
     return acc ? 1 : 0;
 }
 

@@ -102,12 +102,20 @@ struct GaugeSet {
     DevBuf u64;             // [parity][mu][9 double2 planes]
     DevBuf u32;             // [parity][mu][3 float4 planes]
     DevBuf u16, u16b;       // [parity][mu] uint4 plane + uint2 plane
-    // keyed by (kappa csw, kappa mu, open, kappa (cF - 1))
+    // the hopping links of Schroedinger-functional boundaries: the same copies
+    // with every link that touches the boundary slice x_t = 0 set to zero
+    // (built on first use; sf_ready false once the links change)
+    DevBuf u64sf, u32sf, u16sf, u16bsf;
+    bool sf_ready = false;
+    // keyed by (kappa csw, kappa mu, bc, kappa (cF - 1))
     std::map<std::tuple<double, double, int, double>, std::unique_ptr<CloverSet>> clover;
 };
 
 // Storage-format-specific field pointers for one (gauge, clover) pair.
 template <class S> LinkField<S> link_field(const GaugeSet &g, long stride);
+// the links the hopping kernels use under the boundary condition bc (the
+// zeroed copies for LQCD_BC_SF, which clover_get builds)
+template <class S> LinkField<S> hop_links(const GaugeSet &g, long stride, int bc);
 template <class S> CloverField<S> clover_field(const CloverSet &c, bool inverse, long stride);
 // the C blocks of a twisted inverse (null pointers when tau = 0)
 template <class S> CloverField<S> clover_field_c(const CloverSet &c, long stride);
@@ -187,6 +195,8 @@ inline int ntiles_of(long vh) { return int((vh + kBlock - 1) / kBlock); }
 
 // gauge / clover setup (field_ops.cu)
 void gauge_repack(lqcd_lattice_s *lat, GaugeSet &g, const double *U_dev_aos, cudaStream_t st);
+// the clover fields of (g, dp), built on first use; for LQCD_BC_SF also the
+// hopping links of hop_links
 CloverSet &clover_get(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &dp, cudaStream_t st);
 // the boundary phases the hopping kernels use: theta, with theta_t = 0 for an open time boundary
 void hop_theta(const lqcd_dirac_params &dp, double th_re[4], double th_im[4]);
@@ -227,6 +237,8 @@ void pion_contract_aos(lqcd_lattice_s *lat, const double *prop_dev, int src_t, d
                        double *partial, unsigned *counter, cudaStream_t st);
 // the six boundary wall sources delta_{y_t,0} P+ e_j (j = 3 s + c, s < 2), host layout, on the device
 void wall_sources_p_plus(lqcd_lattice_s *lat, double *aos, cudaStream_t st);
+// the six SF boundary sources U_t(0, yvec)^dag P+ e_j on the slice 1, host layout, on the device
+void wall_sources_sf(lqcd_lattice_s *lat, const GaugeSet &g, double *aos, cudaStream_t st);
 // fP[t], fA[t] (device, T doubles each) from six host-layout columns on the device
 void boundary_contract(lqcd_lattice_s *lat, const double *H_dev, double *fP, double *fA, double *partial,
                        unsigned *counter, cudaStream_t st);

@@ -235,6 +235,11 @@ int lqcd_serve_submit(lqcd_server srv, int gauge_id, const lqcd_dirac_params *dp
     if (!srv || !dp || !sp || !src || !ticket) return fail(LQCD_EINVAL, "null argument");
     if (!(dp->kappa >= 0.0) || !std::isfinite(dp->csw) || !std::isfinite(dp->mu))
         return fail(LQCD_EINVAL, "bad dirac params");
+    // SF requests would need the SF hopping links of the shared gauge field,
+    // which the slots do not build concurrently
+    if (dp->bc != LQCD_BC_PERIODIC && dp->bc != LQCD_BC_OPEN)
+        return fail(LQCD_EINVAL, "served requests take periodic or open boundaries");
+    if (dp->bc == LQCD_BC_OPEN && !std::isfinite(dp->cF)) return fail(LQCD_EINVAL, "bad dirac params");
     if (!(sp->tol > 0.0 && sp->tol < 1.0) || sp->maxiter < 1 || sp->precision < LQCD_PREC_FP64 ||
         sp->precision > LQCD_PREC_MIXED_FP16 || sp->inner_tol < 0.0 || sp->inner_tol >= 1.0)
         return fail(LQCD_EINVAL, "bad solver params");

@@ -213,7 +213,7 @@ struct Solver {
         h64.g = lat->geom;
         h64.nrhs = nrhs;
         h64.ntiles = nt;
-        h64.U = link_field<F64>(g, Sd);
+        h64.U = hop_links<F64>(g, Sd, dp.bc);
         hop_theta(dp, h64.th_re, h64.th_im);
         h64.red = red;
         h64.tau = cl.tau;
@@ -222,7 +222,7 @@ struct Solver {
         hw.g = lat->geom;
         hw.nrhs = nrhs;
         hw.ntiles = nt;
-        hw.U = link_field<W>(g, Sd);
+        hw.U = hop_links<W>(g, Sd, dp.bc);
         hop_theta(dp, hw.th_re, hw.th_im);
         hw.red = red;
         hw.tau = cl.tau;
@@ -231,7 +231,7 @@ struct Solver {
         h32.g = lat->geom;
         h32.nrhs = nrhs;
         h32.ntiles = nt;
-        h32.U = link_field<F32>(g, Sd);
+        h32.U = hop_links<F32>(g, Sd, dp.bc);
         hop_theta(dp, h32.th_re, h32.th_im);
         h32.red = red;
         h32.tau = cl.tau;
@@ -690,7 +690,7 @@ void dirac_apply_dev(lqcd_lattice_s *lat, GaugeSet &g, const lqcd_dirac_params &
     a.g = lat->geom;
     a.nrhs = 1;
     a.ntiles = ntiles_of(lat->vh);
-    a.U = link_field<F64>(g, Sd);
+    a.U = hop_links<F64>(g, Sd, dp.bc);
     hop_theta(dp, a.th_re, a.th_im);
     a.clov = clover_field<F64>(cl, false, Sd);
     a.tau = cl.tau;

@@ -178,12 +178,12 @@ def _stream_of(t, stream):
     return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
-BCS = {"periodic": 0, "open": 1}
+BCS = {"periodic": 0, "open": 1, "sf": 2}
 
 
 def dirac_params(kappa, csw, theta=DEFAULT_THETA, mu=0.0, cF=1.0, bc="periodic") -> DiracParams:
     """DiracParam (kappa instead of m0): theta phase factors, twisted mass mu, boundary
-    coefficient cF and the time boundary ("periodic" or "open")."""
+    coefficient cF and the time boundary ("periodic", "open" or "sf")."""
     th = np.asarray(theta, dtype=np.complex128)
     p = DiracParams()
     p.kappa, p.csw, p.mu, p.cF = float(kappa), float(csw), float(mu), float(cF)
@@ -395,7 +395,8 @@ def gauge_download(lat, gauge_id, dims):
 
 
 def boundary_corr(lat, gauge_id, params: DiracParams, solver: SolverParams, dims, want_prop=False):
-    """Boundary-to-bulk f_P, f_A (host arrays) from the six P+ wall sources on slice 0.
+    """Boundary-to-bulk f_P, f_A (host arrays) from the six P+ wall sources on slice 0
+    (on slice 1, carried in by U_t(0)^dag, for bc="sf").
 
     Returns (fP, fA, H or None [6, T, Z, Y, X, 4, 3], infos, status)."""
     lx, ly, lz, lt = dims
