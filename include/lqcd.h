@@ -396,9 +396,12 @@ int lqcd_gauge_download(lqcd_lattice lat, int gauge_id, double *U, int flags, vo
 
 /* Per-kernel statistics since the last lqcd_profile_reset.  launches and
  * bytes count every launch of the kind (bytes = algorithmic bytes: each
- * operand of the launch read or written once, all right-hand sides counted
- * as active).  timed_*: launches bracketed by CUDA events on their stream
- * while timing was enabled, with their summed device time.  Not part of the
+ * operand of the launch read or written once, for the right-hand sides
+ * expected to pass the launch's gate by the last host poll, all of them when
+ * unknown).  Launches replayed from a CUDA graph (small solves below 2^20
+ * site-RHS and batched solves) are counted once, when the graph is
+ * captured, and are not timed.  timed_*: launches bracketed by CUDA events
+ * on their stream while timing was enabled, with their summed device time.  Not part of the
  * paper; this is the library's tracing facility (the paper times methods
  * with TimerOutputs.jl, Sec. 3.4). */
 typedef struct {

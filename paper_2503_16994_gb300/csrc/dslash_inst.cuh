@@ -329,7 +329,7 @@ void launch_hop(const HopArgs<S, L, C> &a, int mode, bool dag, bool norm, cudaSt
     const bool extra = std::is_same<S, F64>::value && !dag && (mode == SELF_PLAIN || mode == CLOV_SUM || mode == RESID);
     if ((mode == HOP_CLOV || mode == SELF_CLOV || extra) && (a.tau == 0.0 || mode == SELF_PLAIN)) {
         FastHop<S> f = make_fast(a);
-        const HopShape sh = hopf_tuned<S>(f, mode, st);
+        const HopShape sh = a.fixed_shape ? HopShape{1, 1, 1, 1} : hopf_tuned<S>(f, mode, st);
         f.gpb = sh.gpb;
         f.minb = sh.minb;
         f.swz = sh.swz;

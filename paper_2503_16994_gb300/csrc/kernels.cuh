@@ -203,6 +203,8 @@ struct HopArgs {
     int gate;                 // RHS j runs only if gate_st[j].status == gate
     Reduce red;
     int nactive = -1;         // launch accounting only: right-hand sides expected to pass the gate (-1: all)
+    bool fixed_shape = false; // true: the scalar one-RHS-per-thread shape, neither tuned nor forced by
+                              // the environment (its bits do not depend on the tuner's choice)
 };
 
 template <class S, class L, class C, typename R, int MU, int SGN>

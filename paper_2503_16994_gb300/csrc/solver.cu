@@ -312,7 +312,8 @@ struct Solver {
     // recomputed rhat (FP64, kept in x_o, which holds nothing else until the
     // odd solution is rebuilt at the end) by the correction gathered since:
     //   rhat <- rhat - scale Dhat e,   x += scale e,   r = rhat / scale,
-    // with Dhat e evaluated by the tuned FP32 kernels straight from e (FP32).
+    // with Dhat e evaluated by the FP32 kernel in its scalar shape (untuned, so the
+    // bits of a solve do not depend on the tuner) straight from e (FP32).
     // Each step adds an error of order 1e-7 |Dhat| |scale e|, i.e. a small
     // multiple of 1e-7 of the residual it starts from, so the error since the
     // last FP64 residual (the anchor) stays of order 1e-7 |anchor|.  It is
@@ -332,6 +333,7 @@ struct Solver {
             a.gate_st = S;
             a.gate = ST_UPDATE;
             a.nactive = hint_update;
+            a.fixed_shape = true;  // the solve's bits must not depend on the tuner's FP32 choice
             a.parity = 1;
             a.in = e;
             a.out = t32;
@@ -548,33 +550,132 @@ struct Solver {
     // schedules every block; the host round trip costs ~15 us against
     // milliseconds of work).  Small batches: gated launches are cheap, so
     // poll every few iterations only.
+    static constexpr int kGraphChunk = 8;  // iterations per poll of small batches
     void iterate(const lqcd_solver_params &sp)
     {
-        const bool poll_each = long(lat->vh) * nrhs >= (1L << 20);
-        const int chunk = poll_each ? 1 : 8;
+        const bool small = long(lat->vh) * nrhs < (1L << 20);
+        if (small && !cancel) {
+            iterate_graph(sp);
+            return;
+        }
         long guard = (long)sp.maxiter + 64;
-        bool finished = false;
-        for (long it = 0; it < guard && !finished && !(cancel && *cancel); it += chunk) {
-            if (!poll_each) hint_active = hint_update = -1;  // statuses change unseen inside a chunk
-            for (int k = 0; k < chunk; ++k) {
-                half1();
-                if (poll_each) {
-                    pull_states();
-                    if (all_finished()) {
-                        finished = true;
-                        break;
-                    }
-                    if (any_status(ST_UPDATE)) update_best();
-                } else {
+        if (small) {
+            // the serving loop's slots (cancel set) share the device with other
+            // host threads and do not capture graphs: chunks of 8 eager
+            // iterations, the (gated) FP64 update after every half 1, one poll
+            // per chunk
+            bool finished = false;
+            for (long it = 0; it < guard && !finished && !(cancel && *cancel); it += kGraphChunk) {
+                hint_active = hint_update = -1;  // statuses change unseen inside a chunk
+                for (int k = 0; k < kGraphChunk; ++k) {
+                    half1();
                     reliable_update();
+                    half2();
                 }
-                half2();
-            }
-            if (!poll_each) {
                 pull_states();
                 finished = all_finished();
             }
+            return;
         }
+        for (long it = 0; it < guard && !(cancel && *cancel); ++it) {
+            half1();
+            pull_states();
+            if (all_finished()) break;
+            if (any_status(ST_UPDATE)) update_best();
+            half2();
+        }
+    }
+
+    // Small batches, where launch latency dominates: chunks of kGraphChunk
+    // iterations replayed from one CUDA graph.  Inside a chunk an RHS that
+    // asks for a residual update pauses (its kernels are gated off); after the
+    // chunk the host runs the update and the paused RHS finish their
+    // iteration (ST_RESUME) before the next replay.  One eager iteration
+    // first, so every kernel shape is autotuned outside the capture.
+    void iterate_graph(const lqcd_solver_params &sp)
+    {
+        // the legacy default stream cannot be captured: run on a stream of our
+        // own, ordered after and before the caller's by events
+        if (st == nullptr || st == cudaStreamLegacy) {
+            cudaStream_t orig = st, own = nullptr;
+            cudaEvent_t ev = nullptr;
+            LQCD_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+            auto restore = [&]() {
+                st = orig;
+                if (ev) cudaEventDestroy(ev);
+                if (own) cudaStreamDestroy(own);
+            };
+            try {
+                LQCD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                LQCD_CUDA(cudaEventRecord(ev, orig));
+                LQCD_CUDA(cudaStreamWaitEvent(own, ev, 0));
+                st = own;
+                iterate_graph(sp);
+                LQCD_CUDA(cudaEventRecord(ev, own));
+                LQCD_CUDA(cudaStreamWaitEvent(orig, ev, 0));
+            } catch (...) {
+                cudaStreamSynchronize(own);
+                restore();
+                throw;
+            }
+            restore();
+            return;
+        }
+        half1();
+        pull_states();
+        if (!all_finished()) {
+            if (any_status(ST_UPDATE)) update_best();
+            half2();
+        }
+        set_resume(ST_RESUME);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        auto cleanup = [&]() {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            exec = nullptr;
+            graph = nullptr;
+        };
+        try {
+            pull_states();
+            const long max_chunks = (long(sp.maxiter) + 64) / kGraphChunk + 2;
+            for (long c = 0; c < max_chunks && !all_finished() && !(cancel && *cancel); ++c) {
+                if (any_status(ST_UPDATE)) {
+                    update_best();
+                    resumed_to_active();
+                }
+                if (!exec) {
+                    LQCD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    try {
+                        hint_active = hint_update = -1;  // statuses change unseen inside a chunk
+                        for (int k = 0; k < kGraphChunk; ++k) {
+                            half1();
+                            half2();
+                        }
+                    } catch (...) {
+                        cudaGraph_t g = nullptr;
+                        cudaStreamEndCapture(st, &g);
+                        if (g) cudaGraphDestroy(g);
+                        throw;
+                    }
+                    LQCD_CUDA(cudaStreamEndCapture(st, &graph));
+                    LQCD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+                }
+                LQCD_CUDA(cudaGraphLaunch(exec, st));
+                pull_states();
+            }
+            // a last update of RHS that paused in the final chunk
+            if (any_status(ST_UPDATE) && !(cancel && *cancel)) {
+                update_best();
+                resumed_to_active();
+                pull_states();
+            }
+        } catch (...) {
+            cleanup();
+            throw;
+        }
+        cleanup();
+        set_resume(ST_ACTIVE);
     }
 
     // x_o, true residuals; RHS whose full-lattice residual misses tol (it
