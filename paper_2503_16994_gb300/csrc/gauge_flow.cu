@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(128) laplace_kernel(Geom g, int p, LinkField<F
     cb_coords(g, p, cb, x);
     spinor<double> acc;
     zero(acc);
+#pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         int y[4];
         shift(g, x, mu, +1, y);
