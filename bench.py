@@ -67,13 +67,13 @@ HOP_BYTES_PER_RHS = {"hop_f16_hopclov": 104.0, "hop_f16_selfclov": 156.0}
 HOP_BYTES_SHARED = {"hop_f16_hopclov": 336.0, "hop_f16_selfclov": 336.0}
 # DRAM bytes (read + write) per site of the FP16 12-RHS hopping kernels from
 # one ncu capture (24^3x48, 331776 sites per parity, staged paired kernel;
-# its summary is kept under profiles/): 509.0 MB for hopclov and 722.0 MB
+# its summary is kept under profiles/): 509.4 MB for hopclov and 721.7 MB
 # for selfclov.  Every operand is read once per site, so the traffic scales
 # with the sites of a launch (the paired kernel the autotuner may pick for
 # hopclov moves the same bytes, 509.8 MB in the same capture setting).
 # Valid only for the kernel sources the capture was taken on (digest
 # below); otherwise the bench reports null.
-HOP_TRAFFIC = {"digest": "59e0902ca05600c9", "hop_f16_hopclov": 509.02e6 / 331776, "hop_f16_selfclov": 721.97e6 / 331776}
+HOP_TRAFFIC = {"digest": "2320439447e6c487", "hop_f16_hopclov": 509.45e6 / 331776, "hop_f16_selfclov": 721.72e6 / 331776}
 KERNEL_SOURCES = ["hopfast.cuh", "lqcd_dev.cuh", "kernels.cuh", "dslash_inst.cuh", "hopp_inst.cuh", "hops.cuh"]
 
 
