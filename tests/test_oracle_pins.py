@@ -1067,3 +1067,114 @@ def test_sf_cgnr_matches_dense_inverse_and_vanishes_on_the_boundary():
     xd = np.linalg.solve(M, b.reshape(-1)).reshape(x.shape)
     assert rel(x, xd) < 1e-11
     assert np.max(np.abs(x[0])) < 1e-14 * np.max(np.abs(x))
+
+
+# --------------------------------------------------------------------------
+# boundary-to-bulk correlators and the twisted-mass solve on rough fields
+# --------------------------------------------------------------------------
+
+def _dense(apply, dims):
+    """The matrix of a linear spinor map, column by column."""
+    n = 12 * int(np.prod(dims))
+    M = np.zeros((n, n), complex)
+    for k in range(n):
+        e = np.zeros(n, complex)
+        e[k] = 1
+        M[:, k] = apply(e.reshape(dims[::-1] + (4, 3))).reshape(-1)
+    return M
+
+
+def _fP_fA(H):
+    """f_P(t) = sum_j sum_xvec |H_j|^2, f_A(t) = -sum_j sum_xvec H_j^dag g_t H_j."""
+    fP = np.einsum("jtzyxsc,jtzyxsc->t", np.conj(H), H).real
+    fA = -np.einsum("jtzyxsc,sr,jtzyxrc->t", np.conj(H), BASIS[3], H).real
+    return fP, fA
+
+
+def _boundary_sources(dims, U, slice_t, link):
+    """W_j, j = 3 s + c: (P+ e_s) times a colour vector on every site of one
+    slice; the colour vector is e_c, or link(U_t(0, yvec)) e_c."""
+    lx, ly, lz, lt = dims
+    Pp = 0.5 * (np.eye(4) + BASIS[3])
+    W = np.zeros((6, lt, lz, ly, lx, 4, 3), complex)
+    for j in range(6):
+        s, c = divmod(j, 3)
+        col = np.zeros((lz, ly, lx, 3), complex)
+        if link is None:
+            col[..., c] = 1
+        else:
+            col[...] = link(U[0, ..., 3, :, :])[..., :, c]
+        W[j, slice_t] = np.einsum("s,zyxa->zyxsa", Pp[:, s], col)
+    return W
+
+
+def _g_trivial_on_slice0(dims, seed):
+    g = inputs.gauge_transform(dims, seed=seed)
+    g[0] = np.eye(3)
+    return g
+
+
+@pytest.mark.parametrize("bc", ["open", "sf"])
+def test_boundary_to_bulk_on_rough_fields(bc):
+    """With clover on a rough field: every H_j is the solve of its source (a
+    dense inverse), f_P and f_A follow from H, f_P > 0 on the dynamical
+    slices, and f_P, f_A do not change under a gauge transformation that is
+    the identity on slice 0 (the boundary). For SF that invariance holds only
+    because the source carries U_t(0)^dag: the same source with U_t(0) in
+    its place (a plausible slip, invisible at unit links) is shown to break it."""
+    dims = (2, 2, 2, 4)
+    kappa, csw, cF = 0.13, 1.4, 1.2
+    th = (np.exp(0.4j), 1, np.exp(-0.7j), 1)
+    U = inputs.gauge_field(dims, 0.45, seed=60)
+    if bc == "open":
+        corr = lambda UU: oracle.boundary_corr(dims, UU, kappa, csw, cF, theta=th, tol=1e-13, want_prop=True)
+        Dop = lambda UU: (lambda v: oracle.dirac_open(dims, UU, kappa, csw, cF, v, theta=th))
+        src = lambda UU, link=None: _boundary_sources(dims, UU, 0, None)
+    else:
+        corr = lambda UU: oracle.boundary_corr_sf(dims, UU, kappa, csw, cF, theta=th, tol=1e-13, want_prop=True)
+        Dop = lambda UU: (lambda v: oracle.dirac_sf(dims, UU, kappa, csw, cF, v, theta=th))
+        dag = lambda u: np.conj(np.swapaxes(u, -1, -2))
+        src = lambda UU, link=dag: _boundary_sources(dims, UU, 1, link)
+    fP, fA, H, iters, res, failed = corr(U)
+    assert failed == 0 and np.all(res <= 1e-13)
+    M = _dense(Dop(U), dims)
+    W = src(U)
+    Hd = np.linalg.solve(M, W.reshape(6, -1).T).T.reshape(W.shape)
+    assert rel(H, Hd) < 1e-11
+    wP, wA = _fP_fA(Hd)
+    assert np.allclose(fP, wP, rtol=1e-11, atol=0)
+    assert np.allclose(fA, wA, rtol=1e-10, atol=1e-12 * np.max(wP))
+    first = 0 if bc == "open" else 1
+    assert np.all(fP[first:] > 0)
+    if bc == "sf":
+        assert fP[0] == 0.0 and fA[0] == 0.0
+    Ug = _transform(U, _g_trivial_on_slice0(dims, 61))
+    gP, gA, *_ = corr(Ug)
+    assert np.allclose(gP, fP, rtol=1e-10, atol=0)
+    assert np.allclose(gA, fA, rtol=1e-9, atol=1e-11 * np.max(fP))
+    if bc == "sf":
+        def fP_of(UU, link):
+            W = src(UU, link)
+            Hs = np.linalg.solve(_dense(Dop(UU), dims), W.reshape(6, -1).T).T.reshape(W.shape)
+            return _fP_fA(Hs)[0]
+        plain = lambda u: u
+        assert np.max(np.abs(fP_of(Ug, plain) - fP_of(U, plain))) > 1e-3 * np.max(fP)
+
+
+def test_twisted_mass_cgnr_matches_dense_inverse():
+    """D(mu) x = b on a rough field with clover and twisted boundary phases;
+    the CGNR solution equals the dense inverse, and mu -> -mu gives the
+    solve of the gamma5-sandwiched adjoint: D(-mu) = g5 D(mu)^dag g5."""
+    dims = (2, 2, 2, 4)
+    kappa, csw, mu = 0.13, 1.4, 0.21
+    th = (np.exp(0.3j), 1, 1, np.exp(1.1j))
+    U = inputs.gauge_field(dims, 0.4, seed=62)
+    b = inputs.spinor_field(dims, seed=63)
+    M = _dense(lambda v: oracle.dirac_tm(dims, U, kappa, csw, mu, v, theta=th), dims)
+    x, it, res, ok = oracle.cgnr_tm(dims, U, kappa, csw, mu, b, theta=th, tol=1e-13)
+    assert ok and res <= 1e-13
+    assert rel(x, np.linalg.solve(M, b.reshape(-1)).reshape(x.shape)) < 1e-11
+    y, it2, res2, ok2 = oracle.cgnr_tm(dims, U, kappa, csw, -mu, b, theta=th, tol=1e-13)
+    g5mat = np.kron(np.eye(int(np.prod(dims))), np.kron(G5, np.eye(3)))
+    Mm = g5mat @ np.conj(M.T) @ g5mat
+    assert ok2 and rel(y, np.linalg.solve(Mm, b.reshape(-1)).reshape(y.shape)) < 1e-11
