@@ -101,3 +101,54 @@ def test_tune_import_validates_before_loading(lib):
     # imported shapes are used (and reported) on the first launch of their key only
     assert lqcd.tune_export() == before
     assert lib.lqcd_tune_import(None) == lqcd.EINVAL
+
+
+def test_every_entry_point_checks_its_arguments_before_the_device(lib):
+    """The remaining entry points: null handles, buffers and counts, and the
+    ranges checked before any device work, return LQCD_EINVAL (and destroying
+    a null server is a no-op) with no GPU present."""
+    import numpy as np
+    E = lqcd.EINVAL
+    dp = lqcd.dirac_params(0.12, 1.0)
+    sp = lqcd.solver_params(tol=1e-10, maxiter=10)
+    info = (lqcd.SolveInfo * 12)()
+    buf = np.zeros(64)
+    p = ctypes.c_void_p(buf.ctypes.data)
+    d4 = (ctypes.c_int * 4)(4, 4, 4, 4)
+    calls = {
+        "schur_apply": lambda: lib.lqcd_schur_apply(None, 0, ctypes.byref(dp), 0, None, None, 1, 1, 0, None),
+        "gauge_free": lambda: lib.lqcd_gauge_free(None, 0),
+        "boundary_corr": lambda: lib.lqcd_boundary_corr(None, 0, ctypes.byref(dp), ctypes.byref(sp), None, None,
+                                                        None, info, 0, None),
+        "gauge_flow": lambda: lib.lqcd_gauge_flow(None, 0, 0.01, 1, None),
+        "fermion_flow": lambda: lib.lqcd_fermion_flow(None, 0, ctypes.byref(dp), None, 1, 0.01, 1, 0, None),
+        "fermion_backflow": lambda: lib.lqcd_fermion_backflow(None, 0, ctypes.byref(dp), None, 1, 0.01, 1, 1, 0,
+                                                              None),
+        "gauge_observables": lambda: lib.lqcd_gauge_observables(None, 0, None, None, None, None, None),
+        "hmc_trajectory": lambda: lib.lqcd_hmc_trajectory(None, 0, 6.0, 0.1, 5, None, 0.5, None, None, None),
+        "gauge_download": lambda: lib.lqcd_gauge_download(None, 0, None, 0, None),
+        "pion_corr_batch (no jobs)": lambda: lib.lqcd_pion_corr_batch(None, 1, ctypes.byref(sp), 0, None),
+        "pion_corr_batch (njobs 0)": lambda: lib.lqcd_pion_corr_batch((lqcd.PionJob * 1)(), 0, ctypes.byref(sp), 0,
+                                                                       None),
+        "pion_corr_batch (chunk)": lambda: lib.lqcd_pion_corr_batch((lqcd.PionJob * 1)(), 1, ctypes.byref(sp), -1,
+                                                                     None),
+        "noalloc (null)": lambda: lib.lqcd_pion_contract_noalloc(None, p, 0, p, None),
+        "noalloc (extent 0)": lambda: lib.lqcd_pion_contract_noalloc((ctypes.c_int * 4)(4, 0, 4, 4), p, 0, p, None),
+        "noalloc (source time)": lambda: lib.lqcd_pion_contract_noalloc(d4, p, 4, p, None),
+        "noalloc (too large)": lambda: lib.lqcd_pion_contract_noalloc((ctypes.c_int * 4)(2, 2, 2, 1 << 20), p, 0,
+                                                                       p, None),
+        "serve_create (null)": lambda: lib.lqcd_serve_create(0, 1 << 30, 4, None),
+        "serve_create (slots)": lambda: lib.lqcd_serve_create(0, 1 << 30, 0, ctypes.byref(ctypes.c_void_p())),
+        "serve_gauge": lambda: lib.lqcd_serve_gauge(None, d4, p, ctypes.byref(ctypes.c_int())),
+        "serve_submit": lambda: lib.lqcd_serve_submit(None, 0, ctypes.byref(dp), ctypes.byref(sp), d4,
+                                                      ctypes.byref(ctypes.c_uint64())),
+        "serve_poll": lambda: lib.lqcd_serve_poll(None, 1, None, None, None, 0),
+        "profile_read": lambda: lib.lqcd_profile_read(None, 0, None),
+        "profile_read (no out)": lambda: lib.lqcd_profile_read(None, 4, ctypes.byref(ctypes.c_int())),
+        "tune_report": lambda: lib.lqcd_tune_report(None, 16),
+        "tune_export (len 0)": lambda: lib.lqcd_tune_export(ctypes.create_string_buffer(4), 0),
+    }
+    for name, call in calls.items():
+        assert call() == E, name
+        assert lqcd.last_error() != "", name
+    assert lib.lqcd_serve_destroy(None) == lqcd.OK
